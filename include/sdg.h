@@ -1,0 +1,226 @@
+/*
+ * sdg.h -- C ABI of the GB300 library for the matrix-free pressure / viscous
+ * solves and the time step of the spectral semi-implicit staggered DG scheme
+ * for the incompressible Navier-Stokes equations (Fambri & Dumbser, Sec. 2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Periodic box [0,L_x] x [0,L_y] (x [0,L_z]) split into n[d] cells per
+ *    direction; degree N (0 <= N <= 11), n1 = N + 1 Gauss-Legendre nodes per
+ *    direction on every main and dual cell (Sec. 2.1).
+ *  - A field is an array of ncell * n1^dim doubles (or floats where stated),
+ *    element-major with the x node fastest:
+ *        idx = (((k*ny + j)*nx + i) * n1^dim) + (l3*n1 + l2)*n1 + l1 .
+ *    Velocity component d is stored on its own dual grid: the block at
+ *    element (i,j,k) is the dual cell shifted by +1/2 along d (Sec. 2.1,
+ *    T_{i+1/2,j,k}, T_{i,j+1/2,k}, T_{i,j,k+1/2}).
+ *  - Pointers marked "device" are device pointers owned by the caller; the
+ *    library never frees them.  Pointers marked "host or device" may be
+ *    either (the copy uses unified addressing).  The handle owns all of its
+ *    internal buffers and frees them in sdg_destroy.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    enqueued on it.  Calls that run an iterative solve synchronise the
+ *    stream while they iterate (convergence is tested on the device and the
+ *    flag is read back), so they return with the result complete.
+ *  - Every entry point returns an sdg_status; on error nothing is guaranteed
+ *    about the outputs.  sdg_strerror gives a message; sdg_last_error gives
+ *    the text of the last failure in this thread.
+ */
+#ifndef SDG_H
+#define SDG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SDG_OK = 0,
+  SDG_ERR_INVALID_ARG = 1,   /* bad size, degree, parameter or NULL pointer */
+  SDG_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  SDG_ERR_NOT_CONVERGED = 3, /* CG hit maxit; x holds the last iterate */
+  SDG_ERR_BREAKDOWN = 4,     /* p^T A p <= 0 or not finite */
+  SDG_ERR_UNSUPPORTED = 5,   /* a configuration this build does not handle */
+  SDG_ERR_TIMEOUT = 6        /* reserved: a bounded device wait ran out */
+} sdg_status;
+
+typedef enum { SDG_FP64 = 0, SDG_MIXED = 1 } sdg_precision;
+
+typedef struct {
+  int dim;       /* 2 or 3 */
+  int n[3];      /* cells per direction; n[2] ignored in 2D; each >= 1 */
+  double L[3];   /* box lengths (> 0); L[2] ignored in 2D */
+} sdg_grid;
+
+typedef struct {
+  int iters;          /* CG iterations (mixed: FP32 iterations) */
+  int outer_iters;    /* mixed: FP64 residual replacements (0 in FP64) */
+  int applies_fp64;   /* operator applications in FP64 */
+  int applies_fp32;   /* operator applications in FP32 */
+  double rel_res;     /* ||r|| / ||b||: recursive residual (FP64 mode) or
+                         true FP64 residual (mixed mode) at exit */
+  int status;         /* sdg_status of this solve */
+} sdg_cg_info;
+
+typedef struct {
+  sdg_cg_info pressure;    /* the pressure solve of the last step */
+  sdg_cg_info viscous[3];  /* the viscous solves of the last step */
+  double pressure_ms;      /* device time of the pressure solves, summed over
+                              the nsteps of the call (CUDA events) */
+  double step_ms;          /* device time of the whole call (CUDA events) */
+  long long pressure_applies; /* operator applications in the pressure solves,
+                                 summed over the nsteps of the call */
+  long long kernel_launches;  /* CUDA kernels the call launched */
+} sdg_step_info;
+
+typedef struct sdg_handle sdg_handle;
+
+/* ---------------------------------------------------------------- set-up */
+
+/* Gauss-Legendre nodes xi[0..N] and weights w[0..N] on [0,1] (Sec. 2.1;
+ * the nodal basis is the Lagrange interpolant through these points).
+ * xi, w: host arrays of N+1 doubles.  Errors: INVALID_ARG. */
+int sdg_nodes(int N, double* xi, double* w);
+
+/* The 1D reference matrices of degree N, each (N+1)x(N+1) row-major, written
+ * to host array `out` in this order: M (mass), R~, L~, R-bar, L-bar
+ * (Eq. matrices), M^L, M^R (Sec. 2.2, L2 projections), H^R, H^L, H^C
+ * (after Eq. pSyst).  `out` holds 10*(N+1)^2 doubles.  Errors: INVALID_ARG. */
+int sdg_matrices(int N, double* out);
+
+/* Create a problem: grid, degree N, viscosity nu >= 0, implicitness
+ * theta in [1/2, 1] (Sec. 2.1, P^{n+theta}), time step dt > 0.  Allocates
+ * the state (U_d, P) and every work buffer on the current CUDA device.
+ * Defaults: see sdg_set_options.
+ * Errors: INVALID_ARG, CUDA. */
+int sdg_create(const sdg_grid* grid, int N, double nu, double theta, double dt,
+               sdg_handle** out);
+int sdg_destroy(sdg_handle* h);
+
+/* Precision mode and CG controls: relative tolerances on ||r||/||b|| for the
+ * pressure and viscous solves, cap on CG iterations per solve.
+ *   SDG_FP64:  plain CG in FP64; stops on the recursive residual.
+ *   SDG_MIXED: CG iterations and operator applications in FP32 with FP64
+ *              reduction of every dot product; the correction is folded into
+ *              the FP64 solution and the true residual b - A x is recomputed
+ *              in FP64 ("reliable update") whenever the FP32 residual has
+ *              dropped by the factor delta since the last update; stops when
+ *              the true FP64 residual meets the tolerance.
+ * Defaults: SDG_FP64, 1e-12, 1e-12, 1000000.  Errors: INVALID_ARG. */
+int sdg_set_options(sdg_handle* h, int precision, double rtol_p, double rtol_v,
+                    int maxit);
+/* Mixed mode: reliable-update factor delta in (0,1) (default 0.1) and the
+ * cap on FP64 residual replacements per solve (default 1000). */
+int sdg_set_mixed_options(sdg_handle* h, double delta, int max_updates);
+
+/* Number of DOF of one field (ncell * n1^dim). */
+long long sdg_ndof(const sdg_handle* h);
+
+/* Copy the state in / out.  u, v (, w in 3D; NULL in 2D), p: host or device
+ * arrays of sdg_ndof doubles.  The initial pressure is used as P^n of the
+ * first step (Eq. pSyst).  Errors: INVALID_ARG, CUDA. */
+int sdg_set_state(sdg_handle* h, const double* u, const double* v,
+                  const double* w, const double* p, void* stream);
+int sdg_get_state(sdg_handle* h, double* u, double* v, double* w, double* p,
+                  void* stream);
+
+/* ---------------------------------------------------------------- operators */
+
+/* y = theta * A' x with A' = dt sum_d (1/dx_d^2) M^{perp d} (H^L x_{i-1} +
+ * H^C x_i + H^R x_{i+1})_d : the left-hand side of Eq. pSyst, periodic.
+ * x, y: device arrays of sdg_ndof elements, double (fp32 = 0) or float
+ * (fp32 = 1); x and y must not overlap.  Errors: INVALID_ARG, CUDA. */
+int sdg_pressure_apply(sdg_handle* h, const void* x, void* y, int fp32,
+                       void* stream);
+
+/* y = (M + nu H) x of Eq. implicitviscosity with the scales of Eqs. uSDG12
+ * and Ux-Uz: M^{xyz} x + nu dt sum_d (1/dx_d^2) M^{perp d} H_d x.
+ * Same arguments as sdg_pressure_apply. */
+int sdg_viscous_apply(sdg_handle* h, const void* x, void* y, int fp32,
+                      void* stream);
+
+/* ---------------------------------------------------------------- solvers */
+
+/* Solve theta A' x = b (Eq. pSyst) by matrix-free CG without
+ * preconditioner (Sec. 2.1), in the handle's precision mode.  b: device,
+ * sdg_ndof doubles, must be orthogonal to the constants (the periodic kernel;
+ * the solve does not project it).  x: device, in = x0, out = solution.
+ * info may be NULL.  Returns the solve status (OK, NOT_CONVERGED, BREAKDOWN)
+ * or INVALID_ARG / CUDA. */
+int sdg_pressure_cg(sdg_handle* h, const double* b, double* x,
+                    sdg_cg_info* info, void* stream);
+
+/* Solve (M + nu H) x = b (Eq. implicitviscosity) by CG; same conventions. */
+int sdg_viscous_cg(sdg_handle* h, const double* b, double* x,
+                   sdg_cg_info* info, void* stream);
+
+/* ---------------------------------------------------------------- step stages */
+
+/* L2 projection of a velocity component d (0..dim-1) from its dual grid to
+ * the main grid (Eq. l2forward) or back (Eq. l2backward).  in, out: device
+ * doubles, sdg_ndof, must not overlap. */
+int sdg_dual_to_main(sdg_handle* h, int d, const double* in, double* out,
+                     void* stream);
+int sdg_main_to_dual(sdg_handle* h, int d, const double* in, double* out,
+                     void* stream);
+
+/* Explicit convection of a main-grid velocity V (dim device arrays) over one
+ * dt by third-order SSP Runge-Kutta with the Rusanov-flux DG operator
+ * (Eqs. Fu-Fw, Sec. 2.2); writes F (dim device arrays). */
+int sdg_convect(sdg_handle* h, const double* const* V, double* const* F,
+                void* stream);
+
+/* Pressure right-hand side from dual-grid velocities U* (dim device arrays)
+ * and the old pressure: b = -sum_d (1/dx_d) M^{perp d} (R-bar U_{i+1/2} -
+ * L-bar U_{i-1/2})_d - (1 - theta) A' P_old (Eqs. pSDG1, pSyst), then b is
+ * shifted to zero mean.  b: device doubles. */
+int sdg_pressure_rhs(sdg_handle* h, const double* const* Ustar,
+                     const double* P_old, double* b, void* stream);
+
+/* Velocity update of Eq. LOvelocityU-W with q = theta P_new +
+ * (1 - theta) P_old: U_d = U*_d - (dt/dx_d) M^-1 (R~ q_{i+1} - L~ q_i)_d.
+ * Ustar, U: dim device arrays each (U may alias Ustar). */
+int sdg_velocity_update(sdg_handle* h, const double* const* Ustar,
+                        const double* P_new, const double* P_old,
+                        double* const* U, void* stream);
+
+/* ---------------------------------------------------------------- time step */
+
+/* Advance the handle's state by nsteps steps of the compact fractional-step
+ * scheme (Eqs. LOdiffusionU-W, LOpressure, LOvelocityU-W): project to the
+ * main grid, SSP-RK3 convection, implicit viscous CG per component, project
+ * back, pressure CG, velocity update, pressure gauge (zero mean).
+ * info may be NULL.  Returns the first non-OK solve status, or OK. */
+int sdg_step(sdg_handle* h, int nsteps, sdg_step_info* info, void* stream);
+
+/* ---------------------------------------------------------------- instrumentation */
+
+/* enable != 0: bracket every launch of the fused CG operator kernel with CUDA
+ * events on the launch stream and accumulate its device time (costs a few
+ * microseconds of host time per launch).  Resets the counters below. */
+int sdg_set_profiling(sdg_handle* h, int enable);
+
+/* Counters since sdg_create or the last sdg_set_profiling: kernels launched
+ * by the handle, and (profiling on) the summed device time in ms and the
+ * number of timed launches of the fused CG operator kernel, index 0 = FP64,
+ * 1 = FP32.  Host outputs; any may be NULL. */
+int sdg_counters(const sdg_handle* h, long long* launches, double* apply_ms,
+                 long long* apply_launches);
+
+/* ---------------------------------------------------------------- diagnostics */
+
+/* Kinetic energy K = (1/|Omega|) int |v|^2/2 (Sec. 2.5) of the handle's
+ * state, by GL quadrature on each dual grid; and the Euclidean norm of the
+ * discrete divergence of Eq. pSDG1.  Host outputs; either may be NULL. */
+int sdg_diagnostics(sdg_handle* h, double* kinetic_energy, double* div_norm,
+                    void* stream);
+
+const char* sdg_strerror(int status);
+const char* sdg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDG_H */

@@ -1,0 +1,647 @@
+// C ABI of libsdg: handle life cycle, operators, CG drivers (FP64 and
+// FP32-inner / FP64-refined) and the fractional time step of Sec. 2.3.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "sdg_internal.h"
+
+using namespace sdg;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+void set_err(const char* fmt, const char* a = "", int line = 0) {
+  std::snprintf(g_err, sizeof(g_err), fmt, a, line);
+}
+
+#define SDG_CK(call)                                                         \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess) {                                                 \
+      set_err("CUDA error %s at sdg_api.cu:%d", cudaGetErrorString(e_), __LINE__); \
+      return SDG_ERR_CUDA;                                                   \
+    }                                                                        \
+  } while (0)
+
+#define SDG_ARG(cond, msg)             \
+  do {                                 \
+    if (!(cond)) {                     \
+      set_err("invalid argument: %s", msg); \
+      return SDG_ERR_INVALID_ARG;      \
+    }                                  \
+  } while (0)
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline SolverState* st_dev(sdg_handle* h, int id) { return h->st + id; }
+inline double* parts(sdg_handle* h, int id) {
+  return h->partials + (size_t)id * (size_t)h->max_blocks * kPartialSlots;
+}
+
+struct Op {
+  double s[3];
+  double cmass;
+};
+
+Op pressure_op(const sdg_handle* h) {
+  Op o{};
+  for (int d = 0; d < h->dim; ++d) o.s[d] = h->theta * h->dt / (h->dx[d] * h->dx[d]);
+  o.cmass = 0.0;
+  return o;
+}
+
+Op viscous_op(const sdg_handle* h) {
+  Op o{};
+  for (int d = 0; d < h->dim; ++d) o.s[d] = h->nu * h->dt / (h->dx[d] * h->dx[d]);
+  o.cmass = 1.0;
+  return o;
+}
+
+}  // namespace
+
+namespace sdg {
+
+cudaError_t launch_apply_f64(const sdg_handle* h, const ApplyArgs<double>& a, cudaStream_t s) {
+  return h->dim == 2 ? apply_dispatch_2d(h, a, s) : apply_dispatch_3d(h, a, s);
+}
+cudaError_t launch_apply_f32(const sdg_handle* h, const ApplyArgs<float>& a, cudaStream_t s) {
+  return h->dim == 2 ? apply_dispatch_2d(h, a, s) : apply_dispatch_3d(h, a, s);
+}
+
+}  // namespace sdg
+
+namespace {
+
+template <typename T>
+cudaError_t apply_plain(const sdg_handle* h, const Op& op, const T* x, T* y, cudaStream_t s) {
+  ApplyArgs<T> a{};
+  a.x = x;
+  a.y = y;
+  for (int d = 0; d < 3; ++d) a.s[d] = op.s[d];
+  a.cmass = op.cmass;
+  a.fuse = 0;
+  if constexpr (sizeof(T) == 8)
+    return launch_apply_f64(h, a, s);
+  else
+    return launch_apply_f32(h, a, s);
+}
+
+#define SDG_K(call)     \
+  do {                  \
+    ++h->launches;      \
+    SDG_CK(call);       \
+  } while (0)
+
+// Host loop of one CG solve in precision T on vectors x (in/out), r, p[2], Ap.
+// Convergence (and, in reliable mode, the need for an FP64 residual
+// replacement) is decided on the device; the host reads the state after each
+// batch of iterations.  Returns with h->st_host[sid] current.
+template <typename T>
+int cg_loop(sdg_handle* h, const Op& op, T* x, T* r, T* const* p, T* Ap, int sid, cudaStream_t s,
+            long long* launched_io) {
+  SolverState* st = st_dev(h, sid);
+  double* pa = parts(h, sid);
+  const long long n = h->g.ndof;
+  long long launched = *launched_io;
+  int batch = 4;
+  const int pk = sizeof(T) == 8 ? 0 : 1;
+  int iter_before = h->st_host[sid].iter;
+  for (;;) {
+    const bool prof = h->profile != 0;
+    const int nb = prof && batch > kProfEvents ? kProfEvents : batch;
+    for (int k = 0; k < nb; ++k) {
+      ApplyArgs<T> a{};
+      a.x = r;
+      a.p_old = p[launched & 1];
+      a.p_out = p[(launched + 1) & 1];
+      a.y = Ap;
+      for (int d = 0; d < 3; ++d) a.s[d] = op.s[d];
+      a.cmass = op.cmass;
+      a.fuse = 1;
+      a.st = st;
+      a.partials = pa;
+      if (prof) SDG_CK(cudaEventRecord(h->pev[2 * k], s));
+      if constexpr (sizeof(T) == 8) {
+        SDG_K(launch_apply_f64(h, a, s));
+        if (prof) SDG_CK(cudaEventRecord(h->pev[2 * k + 1], s));
+        SDG_K(cg_update_f64(x, r, p[(launched + 1) & 1], Ap, n, st, pa, s));
+      } else {
+        SDG_K(launch_apply_f32(h, a, s));
+        if (prof) SDG_CK(cudaEventRecord(h->pev[2 * k + 1], s));
+        SDG_K(cg_update_f32(x, r, p[(launched + 1) & 1], Ap, n, st, pa, s));
+      }
+      ++launched;
+    }
+    SDG_CK(cudaMemcpyAsync(h->st_host + sid, st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+    SDG_CK(cudaStreamSynchronize(s));
+    const SolverState& hs = h->st_host[sid];
+    if (prof) {
+      // the operator ran in iterations iter_before .. hs.iter-1 of this batch
+      const int ran = hs.iter - iter_before;
+      for (int k = 0; k < ran && k < nb; ++k) {
+        float ms = 0.f;
+        SDG_CK(cudaEventElapsedTime(&ms, h->pev[2 * k], h->pev[2 * k + 1]));
+        h->prof_ms[pk] += ms;
+        h->prof_n[pk] += 1;
+      }
+    }
+    iter_before = hs.iter;
+    if (hs.done || hs.pause) break;
+    if (batch < 32) batch *= 2;
+  }
+  *launched_io = launched;
+  return SDG_OK;
+}
+
+void fill_info(sdg_cg_info* info, const SolverState& hs, int outer, int a64, int a32, int status) {
+  if (!info) return;
+  info->iters = hs.iter;
+  info->outer_iters = outer;
+  info->applies_fp64 = a64;
+  info->applies_fp32 = a32;
+  // reliable mode keeps rr scaled by sigma^2 = 1/||b||^2
+  info->rel_res = hs.bnorm2 == 0.0 ? 0.0 : (hs.reliable ? std::sqrt(hs.rr) : std::sqrt(hs.rr / hs.bnorm2));
+  info->status = status;
+}
+
+// Plain FP64 CG on A x = b (A = op), x in/out.
+int solve_fp64(sdg_handle* h, const Op& op, const double* b, double* x, double rtol, int sid,
+               sdg_cg_info* info, cudaStream_t s) {
+  const long long n = h->g.ndof;
+  SDG_K(apply_plain<double>(h, op, x, h->Ap64, s));
+  SDG_K(cg_init_f64(b, h->Ap64, h->r64, n, st_dev(h, sid), parts(h, sid), rtol, h->maxit, s));
+  h->st_host[sid].iter = 0;
+  long long launched = 0;
+  int rc = cg_loop<double>(h, op, x, h->r64, h->p64, h->Ap64, sid, s, &launched);
+  if (rc != SDG_OK) return rc;
+  const SolverState& hs = h->st_host[sid];
+  fill_info(info, hs, 0, 1 + hs.iter, 0, hs.status);
+  return hs.status;
+}
+
+// FP32 CG with FP64 reliable updates (a defect correction that keeps the
+// Krylov direction): the FP32 iteration runs on the sigma-scaled residual and
+// accumulates its correction in x32; whenever the recursive residual has
+// dropped by `delta` since the last update (or reached the tolerance) the
+// correction is added to x in FP64, the true residual b - A x is recomputed
+// in FP64 and replaces the FP32 one.  Converged when the true residual
+// satisfies ||b - A x|| <= rtol ||b||.
+int solve_mixed(sdg_handle* h, const Op& op, const double* b, double* x, double rtol, int sid,
+                sdg_cg_info* info, cudaStream_t s) {
+  const long long n = h->g.ndof;
+  SolverState* st = st_dev(h, sid);
+  double* pa = parts(h, sid);
+  const double delta = h->delta;
+  int a64 = 0, updates = 0;
+  long long launched = 0;
+  // start: r = b - A x0, x32 = 0
+  SDG_CK(cudaMemsetAsync(h->x32, 0, n * sizeof(float), s));
+  SDG_K(apply_plain<double>(h, op, x, h->Ap64, s));
+  ++a64;
+  SDG_K(rel_residual(b, h->Ap64, h->r64, n, st, pa, rtol, h->maxit, delta, 1, s));
+  SDG_K(rel_convert(h->r64, h->r32, n, st, s));
+  h->st_host[sid].iter = 0;
+  int status = SDG_OK;
+  for (;;) {
+    SDG_CK(cudaMemcpyAsync(h->st_host + sid, st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+    SDG_CK(cudaStreamSynchronize(s));
+    if (h->st_host[sid].done) break;
+    int rc = cg_loop<float>(h, op, h->x32, h->r32, h->p32, h->Ap32, sid, s, &launched);
+    if (rc != SDG_OK) return rc;
+    const SolverState hs = h->st_host[sid];
+    // fold the FP32 correction into x and replace the residual (also after
+    // a cap or a breakdown, so that x and the reported residual are current)
+    SDG_K(rel_accumulate(x, h->x32, n, st, s));
+    SDG_K(apply_plain<double>(h, op, x, h->Ap64, s));
+    ++a64;
+    SDG_K(rel_residual(b, h->Ap64, h->r64, n, st, pa, rtol, h->maxit, delta, 0, s));
+    ++updates;
+    if (hs.done || updates >= h->max_updates) {
+      // the FP32 iteration hit maxit or broke down, or the update cap is
+      // reached: report the true residual of the final x
+      SDG_CK(cudaMemcpyAsync(h->st_host + sid, st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+      SDG_CK(cudaStreamSynchronize(s));
+      const SolverState& f = h->st_host[sid];
+      status = f.rr <= f.tol2 ? SDG_OK : (hs.done ? hs.status : SDG_ERR_NOT_CONVERGED);
+      if (status == SDG_OK && hs.status != SDG_OK && f.rr > f.tol2) status = hs.status;
+      break;
+    }
+    SDG_K(rel_convert(h->r64, h->r32, n, st, s));
+  }
+  const SolverState& hs = h->st_host[sid];
+  if (status == SDG_OK) status = hs.status;
+  fill_info(info, hs, updates, a64, hs.iter, status);
+  return status;
+}
+
+int solve(sdg_handle* h, bool pressure, const double* b, double* x, sdg_cg_info* info, cudaStream_t s) {
+  const Op op = pressure ? pressure_op(h) : viscous_op(h);
+  const double rtol = pressure ? h->rtol_p : h->rtol_v;
+  if (h->precision == SDG_MIXED) return solve_mixed(h, op, b, x, rtol, pressure ? kStP32 : kStV32, info, s);
+  return solve_fp64(h, op, b, x, rtol, pressure ? kStP64 : kStV64, info, s);
+}
+
+int pressure_rhs(sdg_handle* h, const double* const* Us, const double* Pold, double* b, cudaStream_t s) {
+  Op op{};
+  for (int d = 0; d < h->dim; ++d) op.s[d] = -(1.0 - h->theta) * h->dt / (h->dx[d] * h->dx[d]);
+  SDG_K(apply_plain<double>(h, op, Pold, h->tmp, s));
+  SDG_K(k_divergence(h, Us, h->tmp, -1.0, b, st_dev(h, kStMisc), parts(h, kStMisc), s));
+  SDG_K(k_shift(b, h->g.ndof, st_dev(h, kStMisc), 0, 1.0 / (double)h->g.ndof, s));
+  return SDG_OK;
+}
+
+template <typename P>
+int alloc(P** p, size_t count) {
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, count * sizeof(P));
+  if (e != cudaSuccess) {
+    set_err("cudaMalloc failed: %s", cudaGetErrorString(e));
+    return SDG_ERR_CUDA;
+  }
+  *p = static_cast<P*>(v);
+  return SDG_OK;
+}
+
+}  // namespace
+
+// =========================================================================== C ABI
+extern "C" {
+
+const char* sdg_strerror(int status) {
+  switch (status) {
+    case SDG_OK: return "ok";
+    case SDG_ERR_INVALID_ARG: return "invalid argument";
+    case SDG_ERR_CUDA: return "CUDA error";
+    case SDG_ERR_NOT_CONVERGED: return "CG did not converge within maxit";
+    case SDG_ERR_BREAKDOWN: return "CG breakdown (p^T A p <= 0 or not finite)";
+    case SDG_ERR_UNSUPPORTED: return "unsupported configuration";
+    case SDG_ERR_TIMEOUT: return "bounded device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+const char* sdg_last_error(void) { return g_err; }
+
+int sdg_nodes(int N, double* xi, double* w) {
+  SDG_ARG(N >= 0 && N <= kMaxN, "N must be in [0, 11]");
+  SDG_ARG(xi && w, "NULL output");
+  gauss_legendre(N + 1, xi, w);
+  return SDG_OK;
+}
+
+int sdg_matrices(int N, double* out) {
+  SDG_ARG(N >= 0 && N <= kMaxN, "N must be in [0, 11]");
+  SDG_ARG(out, "NULL output");
+  Basis1D b;
+  build_basis(N, &b);
+  const int m = (N + 1) * (N + 1);
+  const double* src[10] = {b.M, b.Rt, b.Lt, b.Rb, b.Lb, b.ML, b.MR, b.HR, b.HL, b.HC};
+  for (int k = 0; k < 10; ++k) std::memcpy(out + k * m, src[k], m * sizeof(double));
+  return SDG_OK;
+}
+
+int sdg_create(const sdg_grid* grid, int N, double nu, double theta, double dt, sdg_handle** out) {
+  SDG_ARG(grid && out, "NULL argument");
+  SDG_ARG(grid->dim == 2 || grid->dim == 3, "dim must be 2 or 3");
+  SDG_ARG(N >= 0 && N <= kMaxN, "N must be in [0, 11]");
+  SDG_ARG(nu >= 0.0 && std::isfinite(nu), "nu must be >= 0");
+  SDG_ARG(theta >= 0.5 && theta <= 1.0, "theta must be in [1/2, 1]");
+  SDG_ARG(dt > 0.0 && std::isfinite(dt), "dt must be > 0");
+  for (int d = 0; d < grid->dim; ++d) {
+    SDG_ARG(grid->n[d] >= 1, "cells per direction must be >= 1");
+    SDG_ARG(grid->L[d] > 0.0, "box lengths must be > 0");
+  }
+  sdg_handle* h = new (std::nothrow) sdg_handle();
+  if (!h) return SDG_ERR_CUDA;
+  std::memset(h, 0, sizeof(*h));
+  SDG_CK(cudaGetDevice(&h->device));
+  h->dim = grid->dim;
+  h->g.dim = grid->dim;
+  h->g.n1 = N + 1;
+  h->g.npe = 1;
+  for (int d = 0; d < grid->dim; ++d) h->g.npe *= (N + 1);
+  h->g.ncell = 1;
+  for (int d = 0; d < 3; ++d) {
+    h->g.n[d] = d < grid->dim ? grid->n[d] : 1;
+    h->L[d] = d < grid->dim ? grid->L[d] : 1.0;
+    h->dx[d] = h->L[d] / h->g.n[d];
+    h->g.ncell *= h->g.n[d];
+  }
+  h->g.ndof = h->g.ncell * h->g.npe;
+  h->nu = nu;
+  h->theta = theta;
+  h->dt = dt;
+  h->precision = SDG_FP64;
+  h->rtol_p = h->rtol_v = 1e-12;
+  h->delta = 0.1;
+  h->maxit = 1000000;
+  h->max_updates = 1000;
+  build_basis(N, &h->basis);
+
+  const long long n = h->g.ndof;
+  // the operator kernel has one CTA per element box; the smallest box is one
+  // element, so ncell bounds every grid (and the reduction grid is capped)
+  h->max_blocks = h->g.ncell > kReduceBlocks ? h->g.ncell : kReduceBlocks;
+  int rc = SDG_OK;
+#define A_(p, c) if (rc == SDG_OK) rc = alloc(&(p), (size_t)(c))
+  for (int d = 0; d < h->dim; ++d) {
+    A_(h->U[d], n); A_(h->Vm[d], n); A_(h->S1[d], n); A_(h->S2[d], n);
+    A_(h->F[d], n); A_(h->Vh[d], n); A_(h->Us[d], n);
+  }
+  A_(h->P, n); A_(h->b, n); A_(h->Pn, n); A_(h->tmp, n);
+  A_(h->r64, n); A_(h->p64[0], n); A_(h->p64[1], n); A_(h->Ap64, n);
+  A_(h->x32, n); A_(h->r32, n); A_(h->p32[0], n); A_(h->p32[1], n); A_(h->Ap32, n);
+  A_(h->st, kMaxStates);
+  A_(h->partials, (size_t)kMaxStates * h->max_blocks * kPartialSlots);
+  A_(h->mats, kMatTable);
+#undef A_
+  if (rc != SDG_OK) { sdg_destroy(h); return rc; }
+  if (cudaMallocHost(&h->st_host, kMaxStates * sizeof(SolverState)) != cudaSuccess) {
+    sdg_destroy(h);
+    set_err("cudaMallocHost failed%s", "");
+    return SDG_ERR_CUDA;
+  }
+  // device matrix table
+  double table[kMatTable];
+  std::memset(table, 0, sizeof(table));
+  const Basis1D& B = h->basis;
+  const int n1 = h->g.n1;
+  for (int i = 0; i < n1; ++i) {
+    table[kW * kMatStride + i] = B.w[i];
+    table[kWinv * kMatStride + i] = 1.0 / B.w[i];
+    table[kPhi0 * kMatStride + i] = B.phi0[i];
+    table[kPhi1 * kMatStride + i] = B.phi1[i];
+  }
+  const double* mats[] = {B.M, B.Rt, B.Lt, B.Rb, B.Lb, B.ML, B.MR, B.HR, B.HL, B.HC, B.Dn};
+  const int ids[] = {kM, kRt, kLt, kRb, kLb, kML, kMR, kHR, kHL, kHC, kDn};
+  for (int k = 0; k < 11; ++k) std::memcpy(table + ids[k] * kMatStride, mats[k], n1 * n1 * sizeof(double));
+  cudaError_t e = cudaMemcpy(h->mats, table, sizeof(table), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(h->st, 0, kMaxStates * sizeof(SolverState));
+  for (int d = 0; d < h->dim && e == cudaSuccess; ++d) e = cudaMemset(h->U[d], 0, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(h->P, 0, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(h->p64[0], 0, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(h->p32[0], 0, n * sizeof(float));
+  if (e == cudaSuccess) e = cudaEventCreate(&h->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&h->ev1);
+  if (e == cudaSuccess) e = cudaEventCreate(&h->ev2);
+  if (e == cudaSuccess) e = cudaEventCreate(&h->ev3);
+  for (int k = 0; k < 2 * kProfEvents && e == cudaSuccess; ++k) e = cudaEventCreate(&h->pev[k]);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    set_err("CUDA error %s in sdg_create", cudaGetErrorString(e));
+    sdg_destroy(h);
+    return SDG_ERR_CUDA;
+  }
+  *out = h;
+  return SDG_OK;
+}
+
+int sdg_destroy(sdg_handle* h) {
+  if (!h) return SDG_OK;
+  for (int d = 0; d < 3; ++d) {
+    cudaFree(h->U[d]); cudaFree(h->Vm[d]); cudaFree(h->S1[d]); cudaFree(h->S2[d]);
+    cudaFree(h->F[d]); cudaFree(h->Vh[d]); cudaFree(h->Us[d]);
+  }
+  cudaFree(h->P); cudaFree(h->b); cudaFree(h->Pn); cudaFree(h->tmp);
+  cudaFree(h->r64); cudaFree(h->p64[0]); cudaFree(h->p64[1]); cudaFree(h->Ap64);
+  cudaFree(h->x32); cudaFree(h->r32); cudaFree(h->p32[0]); cudaFree(h->p32[1]); cudaFree(h->Ap32);
+  cudaFree(h->st); cudaFree(h->partials); cudaFree(h->mats);
+  if (h->st_host) cudaFreeHost(h->st_host);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->ev2) cudaEventDestroy(h->ev2);
+  if (h->ev3) cudaEventDestroy(h->ev3);
+  for (int k = 0; k < 2 * kProfEvents; ++k)
+    if (h->pev[k]) cudaEventDestroy(h->pev[k]);
+  delete h;
+  return SDG_OK;
+}
+
+int sdg_set_options(sdg_handle* h, int precision, double rtol_p, double rtol_v, int maxit) {
+  SDG_ARG(h, "NULL handle");
+  SDG_ARG(precision == SDG_FP64 || precision == SDG_MIXED, "precision must be SDG_FP64 or SDG_MIXED");
+  SDG_ARG(rtol_p > 0.0 && rtol_v > 0.0, "tolerances must be > 0");
+  SDG_ARG(maxit >= 1, "maxit must be >= 1");
+  h->precision = precision;
+  h->rtol_p = rtol_p;
+  h->rtol_v = rtol_v;
+  h->maxit = maxit;
+  return SDG_OK;
+}
+
+int sdg_set_mixed_options(sdg_handle* h, double delta, int max_updates) {
+  SDG_ARG(h, "NULL handle");
+  SDG_ARG(delta > 0.0 && delta < 1.0, "delta must be in (0, 1)");
+  SDG_ARG(max_updates >= 1, "max_updates must be >= 1");
+  h->delta = delta;
+  h->max_updates = max_updates;
+  return SDG_OK;
+}
+
+long long sdg_ndof(const sdg_handle* h) { return h ? h->g.ndof : 0; }
+
+int sdg_set_state(sdg_handle* h, const double* u, const double* v, const double* w, const double* p,
+                  void* stream) {
+  SDG_ARG(h && u && v && p, "NULL argument");
+  SDG_ARG(h->dim == 2 || w, "w required in 3D");
+  const size_t bytes = (size_t)h->g.ndof * sizeof(double);
+  const double* src[3] = {u, v, w};
+  for (int d = 0; d < h->dim; ++d) SDG_CK(cudaMemcpyAsync(h->U[d], src[d], bytes, cudaMemcpyDefault, S(stream)));
+  SDG_CK(cudaMemcpyAsync(h->P, p, bytes, cudaMemcpyDefault, S(stream)));
+  SDG_CK(cudaStreamSynchronize(S(stream)));
+  return SDG_OK;
+}
+
+int sdg_get_state(sdg_handle* h, double* u, double* v, double* w, double* p, void* stream) {
+  SDG_ARG(h, "NULL handle");
+  const size_t bytes = (size_t)h->g.ndof * sizeof(double);
+  double* dst[3] = {u, v, w};
+  for (int d = 0; d < h->dim; ++d)
+    if (dst[d]) SDG_CK(cudaMemcpyAsync(dst[d], h->U[d], bytes, cudaMemcpyDefault, S(stream)));
+  if (p) SDG_CK(cudaMemcpyAsync(p, h->P, bytes, cudaMemcpyDefault, S(stream)));
+  SDG_CK(cudaStreamSynchronize(S(stream)));
+  return SDG_OK;
+}
+
+int sdg_pressure_apply(sdg_handle* h, const void* x, void* y, int fp32, void* stream) {
+  SDG_ARG(h && x && y && x != y, "bad arguments");
+  const Op op = pressure_op(h);
+  if (fp32)
+    SDG_K(apply_plain<float>(h, op, static_cast<const float*>(x), static_cast<float*>(y), S(stream)));
+  else
+    SDG_K(apply_plain<double>(h, op, static_cast<const double*>(x), static_cast<double*>(y), S(stream)));
+  return SDG_OK;
+}
+
+int sdg_viscous_apply(sdg_handle* h, const void* x, void* y, int fp32, void* stream) {
+  SDG_ARG(h && x && y && x != y, "bad arguments");
+  const Op op = viscous_op(h);
+  if (fp32)
+    SDG_K(apply_plain<float>(h, op, static_cast<const float*>(x), static_cast<float*>(y), S(stream)));
+  else
+    SDG_K(apply_plain<double>(h, op, static_cast<const double*>(x), static_cast<double*>(y), S(stream)));
+  return SDG_OK;
+}
+
+int sdg_pressure_cg(sdg_handle* h, const double* b, double* x, sdg_cg_info* info, void* stream) {
+  SDG_ARG(h && b && x && b != x, "bad arguments");
+  return solve(h, true, b, x, info, S(stream));
+}
+
+int sdg_viscous_cg(sdg_handle* h, const double* b, double* x, sdg_cg_info* info, void* stream) {
+  SDG_ARG(h && b && x && b != x, "bad arguments");
+  return solve(h, false, b, x, info, S(stream));
+}
+
+int sdg_dual_to_main(sdg_handle* h, int d, const double* in, double* out, void* stream) {
+  SDG_ARG(h && in && out && in != out, "bad arguments");
+  SDG_ARG(d >= 0 && d < h->dim, "direction out of range");
+  SDG_K(k_dual_to_main(h, d, in, out, S(stream)));
+  return SDG_OK;
+}
+
+int sdg_main_to_dual(sdg_handle* h, int d, const double* in, double* out, void* stream) {
+  SDG_ARG(h && in && out && in != out, "bad arguments");
+  SDG_ARG(d >= 0 && d < h->dim, "direction out of range");
+  SDG_K(k_main_to_dual(h, d, in, out, S(stream)));
+  return SDG_OK;
+}
+
+int sdg_convect(sdg_handle* h, const double* const* V, double* const* F, void* stream) {
+  SDG_ARG(h && V && F, "bad arguments");
+  for (int d = 0; d < h->dim; ++d) SDG_ARG(V[d] && F[d], "NULL component");
+  cudaStream_t s = S(stream);
+  SDG_K(k_convect_stage(h, nullptr, V, h->S1, 0.0, 1.0, s));
+  SDG_K(k_convect_stage(h, V, h->S1, h->S2, 0.75, 0.25, s));
+  SDG_K(k_convect_stage(h, V, h->S2, F, 1.0 / 3.0, 2.0 / 3.0, s));
+  return SDG_OK;
+}
+
+int sdg_pressure_rhs(sdg_handle* h, const double* const* Ustar, const double* P_old, double* b, void* stream) {
+  SDG_ARG(h && Ustar && P_old && b, "bad arguments");
+  return pressure_rhs(h, Ustar, P_old, b, S(stream));
+}
+
+int sdg_velocity_update(sdg_handle* h, const double* const* Ustar, const double* P_new, const double* P_old,
+                        double* const* U, void* stream) {
+  SDG_ARG(h && Ustar && P_new && P_old && U, "bad arguments");
+  SDG_K(k_velocity_update(h, Ustar, P_new, P_old, U, S(stream)));
+  return SDG_OK;
+}
+
+int sdg_step(sdg_handle* h, int nsteps, sdg_step_info* info, void* stream) {
+  SDG_ARG(h && nsteps >= 0, "bad arguments");
+  cudaStream_t s = S(stream);
+  const long long n = h->g.ndof;
+  double p_ms = 0.0;
+  long long p_applies = 0;
+  int first_bad = SDG_OK;
+  sdg_cg_info pinfo{}, vinfo[3]{};
+  const long long launches0 = h->launches;
+  SDG_CK(cudaEventRecord(h->ev2, s));
+  for (int step = 0; step < nsteps; ++step) {
+    // 1. dual -> main (Eq. l2forward)
+    for (int d = 0; d < h->dim; ++d) SDG_K(k_dual_to_main(h, d, h->U[d], h->Vm[d], s));
+    // 2. SSP-RK3 of the explicit convection (Eqs. Fu-Fw)
+    SDG_K(k_convect_stage(h, nullptr, h->Vm, h->S1, 0.0, 1.0, s));
+    SDG_K(k_convect_stage(h, h->Vm, h->S1, h->S2, 0.75, 0.25, s));
+    SDG_K(k_convect_stage(h, h->Vm, h->S2, h->F, 1.0 / 3.0, 2.0 / 3.0, s));
+    // 3. implicit viscosity per component (Eq. LOdiffusionU-W)
+    for (int c = 0; c < h->dim; ++c) {
+      SDG_K(k_mass_rhs(h, h->F[c], h->b, h->Vh[c], s));
+      int rc = solve(h, false, h->b, h->Vh[c], &vinfo[c], s);
+      if (rc == SDG_ERR_CUDA || rc == SDG_ERR_INVALID_ARG) return rc;
+      if (rc != SDG_OK && first_bad == SDG_OK) first_bad = rc;
+    }
+    // 4. main -> dual (Eq. l2backward)
+    for (int d = 0; d < h->dim; ++d) SDG_K(k_main_to_dual(h, d, h->Vh[d], h->Us[d], s));
+    // 5. pressure system (Eqs. pSyst, LOpressure), x0 = P^n
+    {
+      int rc = pressure_rhs(h, h->Us, h->P, h->b, s);
+      if (rc != SDG_OK) return rc;
+    }
+    SDG_CK(cudaMemcpyAsync(h->Pn, h->P, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    SDG_CK(cudaEventRecord(h->ev0, s));
+    {
+      int rc = solve(h, true, h->b, h->Pn, &pinfo, s);
+      if (rc == SDG_ERR_CUDA || rc == SDG_ERR_INVALID_ARG) return rc;
+      if (rc != SDG_OK && first_bad == SDG_OK) first_bad = rc;
+    }
+    SDG_CK(cudaEventRecord(h->ev1, s));
+    SDG_CK(cudaEventSynchronize(h->ev1));
+    float ms = 0.f;
+    SDG_CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    p_ms += ms;
+    p_applies += pinfo.applies_fp64 + pinfo.applies_fp32;
+    // 6. gauge: zero physical mean of P^{n+1}
+    SDG_K(k_weighted_sum(h, h->Pn, nullptr, st_dev(h, kStMisc), 1, parts(h, kStMisc), s));
+    SDG_K(k_shift(h->Pn, n, st_dev(h, kStMisc), 1, 1.0 / (double)h->g.ncell, s));
+    // 7. velocity update with q = theta P^{n+1} + (1-theta) P^n (Eq. LOvelocityU-W)
+    SDG_K(k_velocity_update(h, h->Us, h->Pn, h->P, h->U, s));
+    double* t = h->P;
+    h->P = h->Pn;
+    h->Pn = t;
+  }
+  SDG_CK(cudaEventRecord(h->ev3, s));
+  SDG_CK(cudaEventSynchronize(h->ev3));
+  float total = 0.f;
+  SDG_CK(cudaEventElapsedTime(&total, h->ev2, h->ev3));
+  if (info) {
+    info->pressure = pinfo;
+    for (int c = 0; c < 3; ++c) info->viscous[c] = vinfo[c];
+    info->pressure_ms = p_ms;
+    info->step_ms = total;
+    info->pressure_applies = p_applies;
+    info->kernel_launches = h->launches - launches0;
+  }
+  return first_bad;
+}
+
+int sdg_set_profiling(sdg_handle* h, int enable) {
+  SDG_ARG(h, "NULL handle");
+  h->profile = enable ? 1 : 0;
+  h->launches = 0;
+  h->prof_ms[0] = h->prof_ms[1] = 0.0;
+  h->prof_n[0] = h->prof_n[1] = 0;
+  return SDG_OK;
+}
+
+int sdg_counters(const sdg_handle* h, long long* launches, double* apply_ms, long long* apply_launches) {
+  SDG_ARG(h, "NULL handle");
+  if (launches) *launches = h->launches;
+  if (apply_ms) { apply_ms[0] = h->prof_ms[0]; apply_ms[1] = h->prof_ms[1]; }
+  if (apply_launches) { apply_launches[0] = h->prof_n[0]; apply_launches[1] = h->prof_n[1]; }
+  return SDG_OK;
+}
+
+int sdg_diagnostics(sdg_handle* h, double* kinetic_energy, double* div_norm, void* stream) {
+  SDG_ARG(h, "NULL handle");
+  cudaStream_t s = S(stream);
+  SolverState* st = st_dev(h, kStMisc);
+  double* pa = parts(h, kStMisc);
+  double ke = 0.0;
+  if (kinetic_energy) {
+    for (int d = 0; d < h->dim; ++d) {
+      SDG_K(k_weighted_sum(h, h->U[d], h->U[d], st, 2, pa, s));
+      SDG_CK(cudaMemcpyAsync(h->st_host + kStMisc, st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+      SDG_CK(cudaStreamSynchronize(s));
+      ke += h->st_host[kStMisc].red[2];
+    }
+    double cellvol = 1.0, vol = 1.0;
+    for (int d = 0; d < h->dim; ++d) { cellvol *= h->dx[d]; vol *= h->L[d]; }
+    *kinetic_energy = 0.5 * cellvol * ke / vol;
+  }
+  if (div_norm) {
+    SDG_K(k_divergence(h, h->U, nullptr, 1.0, h->tmp, st, pa, s));
+    SDG_K(k_norm2(h->tmp, h->g.ndof, st, 3, pa, s));
+    SDG_CK(cudaMemcpyAsync(h->st_host + kStMisc, st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+    SDG_CK(cudaStreamSynchronize(s));
+    *div_norm = std::sqrt(h->st_host[kStMisc].red[3]);
+  }
+  return SDG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,329 @@
+// Element-tile kernel of the block penta- (2D) / hepta- (3D) diagonal
+// staggered DG operator (Eq. pSyst):
+//   y = cmass * W x + sum_d s_d M^{perp d} (H^L x_{i-1} + H^C x_i + H^R x_{i+1})_d
+// applied dimension by dimension as 1D n1 x n1 contractions (Eq. tensorP1).
+//
+// One CTA owns a TX x TY (x TZ) box of elements.  It stages the box plus the
+// one-element face halo in each direction (corners are never needed) in
+// shared memory with coalesced vector loads, then runs one pass per
+// direction in which every thread owns one 1D line of one element: it holds
+// the 3 n1 line values (left neighbour, centre, right neighbour) in
+// registers and forms the n1 outputs with the 1D blocks.  All threads of a
+// warp use the same matrix entry at the same instruction, so the blocks are
+// read straight from the kernel-parameter constant bank.  Partial results of
+// the passes meet in a shared-memory accumulator; the last step stores the
+// box with vector stores and (CG mode) reduces p^T A p.
+#pragma once
+
+#include <type_traits>
+
+#include "sdg_device.cuh"
+
+namespace sdg {
+
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+// Element box per CTA for each (dim, n1): about 200-300 threads (one per line).
+template <int DIM, int N1>
+struct Tile {
+  static constexpr int TX = DIM == 2 ? (N1 <= 1 ? 16 : N1 <= 2 ? 16 : N1 <= 4 ? 8 : N1 <= 8 ? 8 : 4)
+                                     : (N1 <= 1 ? 8 : N1 <= 2 ? 4 : N1 <= 3 ? 4 : N1 <= 4 ? 4 : N1 <= 10 ? 2 : 1);
+  static constexpr int TY = DIM == 2 ? (N1 <= 1 ? 16 : N1 <= 2 ? 8 : N1 <= 4 ? 8 : N1 <= 8 ? 4 : 4)
+                                     : (N1 <= 1 ? 8 : N1 <= 2 ? 4 : N1 <= 3 ? 4 : N1 <= 4 ? 2 : N1 <= 8 ? 2 : 1);
+  static constexpr int TZ = DIM == 2 ? 1
+                                     : (N1 <= 1 ? 4 : N1 <= 2 ? 4 : N1 <= 3 ? 2 : N1 <= 4 ? 2 : N1 <= 5 ? 2 : 1);
+  static constexpr int TE = TX * TY * TZ;
+  static constexpr int NPE = ipow(N1, DIM);
+  static constexpr int LINES = ipow(N1, DIM - 1);
+  static constexpr int THREADS = TE * LINES;
+  static constexpr int NSLOT = TE + 2 * TY * TZ + 2 * TX * TZ + (DIM == 3 ? 2 * TX * TY : 0);
+};
+
+template <typename T, int N1>
+struct Coef {
+  T HL[N1 * N1], HC[N1 * N1], HR[N1 * N1];
+};
+
+template <typename T, int DIM, int N1>
+struct ApplyParams {
+  Coef<T, N1> c;
+  T w[N1];
+  const T* x;
+  const T* p_old;
+  T* p_out;
+  T* y;
+  T s[3];
+  T cmass;
+  int n[3];
+  int ntile[3];
+  int fuse;
+  SolverState* st;
+  double* partials;
+};
+
+template <typename T>
+struct VecOf;
+template <>
+struct VecOf<double> { using V = double2; static constexpr int W = 2; };
+template <>
+struct VecOf<float> { using V = float4; static constexpr int W = 4; };
+
+template <typename T, int NPE>
+struct Vec {
+  static constexpr bool kOk = (NPE * (int)sizeof(T)) % 16 == 0;
+  static constexpr int W = kOk ? VecOf<T>::W : 1;
+};
+
+// Shared-memory slot of tile-local element (lx,ly,lz), which may lie one
+// step outside the valid box [0,V) along exactly one direction.
+template <int TX, int TY, int TZ>
+__device__ __forceinline__ int slot_of(int lx, int ly, int lz, int VX, int VY, int VZ) {
+  constexpr int TE = TX * TY * TZ;
+  constexpr int XF = TE, YF = XF + 2 * TY * TZ, ZF = YF + 2 * TX * TZ;
+  if (lx < 0) return XF + lz * TY + ly;
+  if (lx >= VX) return XF + TY * TZ + lz * TY + ly;
+  if (ly < 0) return YF + lz * TX + lx;
+  if (ly >= VY) return YF + TX * TZ + lz * TX + lx;
+  if (lz < 0) return ZF + ly * TX + lx;
+  if (lz >= VZ) return ZF + TX * TY + ly * TX + lx;
+  return (lz * TY + ly) * TX + lx;
+}
+
+// Global element coordinates held by slot s; false if the slot is unused.
+template <int DIM, int TX, int TY, int TZ>
+__device__ __forceinline__ bool slot_elem(int s, const int o[3], int VX, int VY, int VZ, const int n[3],
+                                          int g[3]) {
+  constexpr int TE = TX * TY * TZ;
+  int lx, ly, lz;
+  if (s < TE) {
+    lx = s % TX;
+    ly = (s / TX) % TY;
+    lz = s / (TX * TY);
+    if (lx >= VX || ly >= VY || lz >= VZ) return false;
+  } else if ((s -= TE) < 2 * TY * TZ) {
+    const int side = s / (TY * TZ), r = s % (TY * TZ);
+    ly = r % TY;
+    lz = r / TY;
+    if (ly >= VY || lz >= VZ) return false;
+    lx = side ? VX : -1;
+  } else if ((s -= 2 * TY * TZ) < 2 * TX * TZ) {
+    const int side = s / (TX * TZ), r = s % (TX * TZ);
+    lx = r % TX;
+    lz = r / TX;
+    if (lx >= VX || lz >= VZ) return false;
+    ly = side ? VY : -1;
+  } else {
+    if (DIM != 3) return false;
+    s -= 2 * TX * TZ;
+    const int side = s / (TX * TY), r = s % (TX * TY);
+    lx = r % TX;
+    ly = r / TX;
+    if (lx >= VX || ly >= VY) return false;
+    lz = side ? VZ : -1;
+  }
+  int gx = o[0] + lx, gy = o[1] + ly, gz = o[2] + lz;
+  gx = gx < 0 ? gx + n[0] : (gx >= n[0] ? gx - n[0] : gx);
+  gy = gy < 0 ? gy + n[1] : (gy >= n[1] ? gy - n[1] : gy);
+  gz = gz < 0 ? gz + n[2] : (gz >= n[2] ? gz - n[2] : gz);
+  g[0] = gx;
+  g[1] = gy;
+  g[2] = gz;
+  return true;
+}
+
+template <typename T, int DIM, int N1>
+__global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
+    k_apply(const __grid_constant__ ApplyParams<T, DIM, N1> a) {
+  using TS = Tile<DIM, N1>;
+  constexpr int TX = TS::TX, TY = TS::TY, TZ = TS::TZ, TE = TS::TE;
+  constexpr int NPE = TS::NPE, LINES = TS::LINES, NSLOT = TS::NSLOT;
+  constexpr int VW = Vec<T, NPE>::W;
+  constexpr int NV = NPE / VW;  // vectors per element
+  using V = typename std::conditional<VW == 1, T, typename VecOf<T>::V>::type;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s_in = reinterpret_cast<T*>(smem_raw);  // NSLOT * NPE
+  T* s_out = s_in + NSLOT * NPE;             // TE * NPE
+  __shared__ T s_w[N1];
+
+  const bool fuse = a.fuse != 0;
+  bool first = false;
+  T beta = T(0);
+  if (fuse) {
+    if (a.st->done || a.st->pause) return;  // uniform: written by the previous kernel
+    first = (a.st->iter == 0);
+    beta = first ? T(0) : T(a.st->rr / a.st->rr_old);
+  }
+  if (threadIdx.x < N1) s_w[threadIdx.x] = a.w[threadIdx.x];
+
+  // tile origin and valid extents
+  const int bx = blockIdx.x % a.ntile[0];
+  const int by = (blockIdx.x / a.ntile[0]) % a.ntile[1];
+  const int bz = blockIdx.x / (a.ntile[0] * a.ntile[1]);
+  const int o[3] = {bx * TX, by * TY, bz * TZ};
+  const int VX = min(TX, a.n[0] - o[0]);
+  const int VY = min(TY, a.n[1] - o[1]);
+  const int VZ = DIM == 3 ? min(TZ, a.n[2] - o[2]) : 1;
+
+  // ---- stage box + face halo (coalesced, vectorised) ----
+  for (int v = threadIdx.x; v < NSLOT * NV; v += blockDim.x) {
+    const int s = v / NV, off = v - s * NV;
+    int g[3];
+    if (!slot_elem<DIM, TX, TY, TZ>(s, o, VX, VY, VZ, a.n, g)) continue;
+    const long long ge = ((long long)g[2] * a.n[1] + g[1]) * a.n[0] + g[0];
+    const size_t gi = (size_t)ge * NV + off;
+    V val;
+    if (!fuse) {
+      val = reinterpret_cast<const V*>(a.x)[gi];
+    } else {
+      V r = reinterpret_cast<const V*>(a.x)[gi];
+      if (first) {
+        val = r;
+      } else {
+        V po = reinterpret_cast<const V*>(a.p_old)[gi];
+        const T* rp = reinterpret_cast<const T*>(&r);
+        const T* pp = reinterpret_cast<const T*>(&po);
+        T* vp = reinterpret_cast<T*>(&val);
+#pragma unroll
+        for (int k = 0; k < VW; ++k) vp[k] = rp[k] + beta * pp[k];
+      }
+      if (s < TE) reinterpret_cast<V*>(a.p_out)[gi] = val;
+    }
+    reinterpret_cast<V*>(s_in)[s * NV + off] = val;
+  }
+  __syncthreads();
+
+  // ---- one pass per direction ----
+  const int t = threadIdx.x;
+  const int te = t / LINES, lam = t - te * LINES;
+  const int lx = te % TX, ly = (te / TX) % TY, lz = te / (TX * TY);
+  const bool active = (lx < VX) && (ly < VY) && (lz < VZ);
+
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    if (active) {
+      // fixed local indices of this line and its base offset / stride
+      int base, stride;
+      T wp;
+      if (DIM == 2) {
+        // d = 0: lam = l2 (row), d = 1: lam = l1 (column)
+        base = d == 0 ? lam * N1 : lam;
+        stride = d == 0 ? 1 : N1;
+        wp = s_w[lam];
+      } else {
+        const int q0 = lam % N1, q1 = lam / N1;
+        if (d == 0) { base = q0 * N1 + q1 * N1 * N1; stride = 1; }
+        else if (d == 1) { base = q0 + q1 * N1 * N1; stride = N1; }
+        else { base = q0 + q1 * N1; stride = N1 * N1; }
+        wp = s_w[q0] * s_w[q1];
+      }
+      const int sc = (lz * TY + ly) * TX + lx;
+      const int sl = slot_of<TX, TY, TZ>(lx - (d == 0), ly - (d == 1), lz - (d == 2), VX, VY, VZ);
+      const int sr = slot_of<TX, TY, TZ>(lx + (d == 0), ly + (d == 1), lz + (d == 2), VX, VY, VZ);
+      T xl[N1], xc[N1], xr[N1];
+#pragma unroll
+      for (int k = 0; k < N1; ++k) {
+        xl[k] = s_in[sl * NPE + base + k * stride];
+        xc[k] = s_in[sc * NPE + base + k * stride];
+        xr[k] = s_in[sr * NPE + base + k * stride];
+      }
+      const T f = a.s[d] * wp;
+      T* out = s_out + te * NPE + base;
+#pragma unroll
+      for (int m = 0; m < N1; ++m) {
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+          acc = fma(a.c.HL[m * N1 + k], xl[k], acc);
+          acc = fma(a.c.HC[m * N1 + k], xc[k], acc);
+          acc = fma(a.c.HR[m * N1 + k], xr[k], acc);
+        }
+        T val = f * acc;
+        if (d == 0) {
+          val = fma(a.cmass * wp * s_w[m], xc[m], val);
+          out[m * stride] = val;
+        } else {
+          out[m * stride] += val;
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- store the box (vectorised) and reduce p^T A p ----
+  double dot = 0.0;
+  for (int v = threadIdx.x; v < TE * NV; v += blockDim.x) {
+    const int e = v / NV, off = v - e * NV;
+    const int ex = e % TX, ey = (e / TX) % TY, ez = e / (TX * TY);
+    if (ex >= VX || ey >= VY || ez >= VZ) continue;
+    const long long ge = ((long long)(o[2] + ez) * a.n[1] + (o[1] + ey)) * a.n[0] + (o[0] + ex);
+    const V yv = reinterpret_cast<const V*>(s_out)[e * NV + off];
+    reinterpret_cast<V*>(a.y)[(size_t)ge * NV + off] = yv;
+    if (fuse) {
+      const V pv = reinterpret_cast<const V*>(s_in)[e * NV + off];
+      const T* yp = reinterpret_cast<const T*>(&yv);
+      const T* pp = reinterpret_cast<const T*>(&pv);
+#pragma unroll
+      for (int k = 0; k < VW; ++k) dot += (double)pp[k] * (double)yp[k];
+    }
+  }
+  if (fuse) {
+    double v1[1] = {dot}, tot[1];
+    if (grid_sum<1>(v1, a.partials, &a.st->counter, tot)) {
+      if (threadIdx.x == 0) {
+        SolverState* st = a.st;
+        const double pAp = tot[0];
+        st->pAp = pAp;
+        if (!(pAp > 0.0) || !isfinite(pAp)) {
+          st->done = 1;
+          st->status = SDG_ERR_BREAKDOWN;
+          st->alpha = 0.0;
+        } else {
+          st->alpha = st->rr / pAp;
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int DIM, int N1>
+cudaError_t launch_apply_t(const sdg_handle* h, const ApplyArgs<T>& in, cudaStream_t stream) {
+  using TS = Tile<DIM, N1>;
+  ApplyParams<T, DIM, N1> p;
+  const Basis1D& b = h->basis;
+  for (int i = 0; i < N1 * N1; ++i) {
+    p.c.HL[i] = (T)b.HL[i];
+    p.c.HC[i] = (T)b.HC[i];
+    p.c.HR[i] = (T)b.HR[i];
+  }
+  for (int i = 0; i < N1; ++i) p.w[i] = (T)b.w[i];
+  p.x = in.x;
+  p.p_old = in.p_old;
+  p.p_out = in.p_out;
+  p.y = in.y;
+  for (int d = 0; d < 3; ++d) p.s[d] = (T)in.s[d];
+  p.cmass = (T)in.cmass;
+  p.n[0] = h->g.n[0];
+  p.n[1] = h->g.n[1];
+  p.n[2] = DIM == 3 ? h->g.n[2] : 1;
+  p.ntile[0] = (p.n[0] + TS::TX - 1) / TS::TX;
+  p.ntile[1] = (p.n[1] + TS::TY - 1) / TS::TY;
+  p.ntile[2] = (p.n[2] + TS::TZ - 1) / TS::TZ;
+  p.fuse = in.fuse;
+  p.st = in.st;
+  p.partials = in.partials;
+  const long long nblk = (long long)p.ntile[0] * p.ntile[1] * p.ntile[2];
+  if (nblk > h->max_blocks) return cudaErrorInvalidConfiguration;
+  const size_t smem = (size_t)(TS::NSLOT + TS::TE) * TS::NPE * sizeof(T);
+  static bool attr_set = false;  // per instantiation; smem need is fixed
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_apply<T, DIM, N1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_apply<T, DIM, N1><<<(unsigned)nblk, TS::THREADS, smem, stream>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace sdg

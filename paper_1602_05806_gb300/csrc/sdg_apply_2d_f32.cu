@@ -1,0 +1,24 @@
+// Instantiations of the element-tile operator kernel for dim = 2, float.
+#include "sdg_apply.cuh"
+
+namespace sdg {
+
+cudaError_t apply_dispatch_2d(const sdg_handle* h, const ApplyArgs<float>& a, cudaStream_t s) {
+  switch (h->g.n1) {
+    case 1: return launch_apply_t<float, 2, 1>(h, a, s);
+    case 2: return launch_apply_t<float, 2, 2>(h, a, s);
+    case 3: return launch_apply_t<float, 2, 3>(h, a, s);
+    case 4: return launch_apply_t<float, 2, 4>(h, a, s);
+    case 5: return launch_apply_t<float, 2, 5>(h, a, s);
+    case 6: return launch_apply_t<float, 2, 6>(h, a, s);
+    case 7: return launch_apply_t<float, 2, 7>(h, a, s);
+    case 8: return launch_apply_t<float, 2, 8>(h, a, s);
+    case 9: return launch_apply_t<float, 2, 9>(h, a, s);
+    case 10: return launch_apply_t<float, 2, 10>(h, a, s);
+    case 11: return launch_apply_t<float, 2, 11>(h, a, s);
+    case 12: return launch_apply_t<float, 2, 12>(h, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace sdg

@@ -1,0 +1,29 @@
+// 1D reference-element algebra of degree N on [0,1] (Sec. 2.1, Eq. matrices;
+// Sec. 2.2, L2 projections).  All matrices row-major n1 x n1, entry [p][q] at
+// p*n1 + q, with p the test-function index and q the unknown index.
+#pragma once
+
+namespace sdg {
+
+constexpr int kMaxN = 11;
+constexpr int kMaxN1 = kMaxN + 1;
+
+struct Basis1D {
+  int N, n1;
+  double xi[kMaxN1], w[kMaxN1];           // GL nodes / weights on [0,1]
+  double phi0[kMaxN1], phi1[kMaxN1];      // phi_m(0), phi_m(1)
+  double M[kMaxN1 * kMaxN1];              // mass matrix (diagonal = w)
+  double Rt[kMaxN1 * kMaxN1], Lt[kMaxN1 * kMaxN1];   // R~, L~
+  double Rb[kMaxN1 * kMaxN1], Lb[kMaxN1 * kMaxN1];   // R-bar, L-bar
+  double ML[kMaxN1 * kMaxN1], MR[kMaxN1 * kMaxN1];   // M^L, M^R
+  double HR[kMaxN1 * kMaxN1], HL[kMaxN1 * kMaxN1], HC[kMaxN1 * kMaxN1];
+  double Dn[kMaxN1 * kMaxN1];             // Dn[k][m] = phi_m'(xi_k)
+};
+
+// n-point Gauss-Legendre rule on [0,1], nodes ascending.
+void gauss_legendre(int n, double* xi, double* w);
+
+// Fill every matrix of degree N (0 <= N <= kMaxN).  Returns 0 or -1.
+int build_basis(int N, Basis1D* b);
+
+}  // namespace sdg

@@ -1,0 +1,108 @@
+// Device helpers: block / grid reductions with a deterministic last-block
+// finish, and index arithmetic of the element-major field layout.
+#pragma once
+
+#include "sdg_internal.h"
+
+namespace sdg {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum K values over the block; the totals end up in out[] of every thread.
+// s_red: shared scratch of at least 32*K doubles.  Must be reached by all
+// threads of the block.
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double* s_red, double (&out)[K]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double t = warp_sum(v[k]);
+    if (lane == 0) s_red[k * 32 + wid] = t;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double t = (lane < nw) ? s_red[k * 32 + lane] : 0.0;
+    out[k] = warp_sum(t);  // every warp computes the same total
+  }
+  __syncthreads();
+}
+
+// Grid-wide sum with a deterministic finish: every block writes its partial
+// sums to partials[block*kPartialSlots + k]; the last block to arrive adds
+// them in block order and returns true (in all of its threads) with the
+// totals in tot[].  Other blocks return false.  The ticket counter is reset
+// by the last block, so the same counter serves the next launch.
+template <int K>
+__device__ __forceinline__ bool grid_sum(double (&v)[K], double* partials, unsigned int* counter,
+                                         double (&tot)[K]) {
+  static_assert(K <= kPartialSlots, "too many reduction slots");
+  __shared__ double s_red[32 * K];
+  __shared__ int s_last;
+  double b[K];
+  block_sum<K>(v, s_red, b);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) partials[(size_t)blockIdx.x * kPartialSlots + k] = b[k];
+    __threadfence();
+    unsigned int t = atomicAdd(counter, 1u);
+    s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.0;
+  for (unsigned int i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] += __ldcg(&partials[(size_t)i * kPartialSlots + k]);
+  }
+  block_sum<K>(acc, s_red, tot);
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+// ---- layout ----------------------------------------------------------------
+__device__ __forceinline__ void split_index(const Geo& g, long long idx, int e[3], int l[3]) {
+  const long long el = idx / g.npe;
+  int loc = (int)(idx - el * g.npe);
+  l[0] = loc % g.n1;
+  loc /= g.n1;
+  l[1] = loc % g.n1;
+  l[2] = loc / g.n1;
+  e[0] = (int)(el % g.n[0]);
+  const long long r = el / g.n[0];
+  e[1] = (int)(r % g.n[1]);
+  e[2] = (int)(r / g.n[1]);
+  if (g.dim == 2) { l[2] = 0; e[2] = 0; }
+}
+
+__device__ __forceinline__ long long elem_of(const Geo& g, const int e[3]) {
+  return ((long long)e[2] * g.n[1] + e[1]) * g.n[0] + e[0];
+}
+
+__device__ __forceinline__ int local_of(const Geo& g, const int l[3]) {
+  return (l[2] * g.n1 + l[1]) * g.n1 + l[0];
+}
+
+// element index of e shifted by s (+-1) along d, periodic
+__device__ __forceinline__ long long elem_shift(const Geo& g, const int e[3], int d, int s) {
+  int f[3] = {e[0], e[1], e[2]};
+  f[d] += s;
+  if (f[d] < 0) f[d] += g.n[d];
+  if (f[d] >= g.n[d]) f[d] -= g.n[d];
+  return elem_of(g, f);
+}
+
+// local node stride of direction d
+__device__ __forceinline__ int lstride(const Geo& g, int d) {
+  return d == 0 ? 1 : (d == 1 ? g.n1 : g.n1 * g.n1);
+}
+
+}  // namespace sdg

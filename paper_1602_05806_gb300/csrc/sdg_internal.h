@@ -1,0 +1,178 @@
+// Internal declarations shared by the CUDA translation units of libsdg.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/sdg.h"
+#include "sdg_basis.h"
+
+namespace sdg {
+
+// Device-resident control block of one iterative solve.  Written only by
+// the last block of a reducing kernel, read by every block of the next
+// kernel on the same stream (kernel boundaries order the accesses).
+struct SolverState {
+  double rr;        // current ||r||^2 (recursive)
+  double rr_old;    // previous ||r||^2
+  double pAp;       // p^T A p of the current iteration
+  double alpha;     // rr / pAp
+  double bnorm2;    // ||b||^2
+  double tol2;      // (rtol ||b||)^2
+  double mean;      // mixed: mean of the FP64 residual (removed: periodic kernel)
+  double sigma;     // mixed: FP32 vectors hold sigma * (FP64 quantities), sigma = 1/||b||
+  double maxrr;     // mixed: largest recursive ||r||^2 since the last reliable update
+  double delta2;    // mixed: reliable update when rr < delta2 * maxrr
+  double red[4];    // results of plain reductions
+  int iter;         // iterations done
+  int maxit;
+  int done;         // 1 once converged / failed / capped
+  int status;       // sdg_status of this solve
+  int reliable;     // 1: FP32 iterations pause for FP64 residual replacement
+  int pause;        // set by the update kernel when a reliable update is due
+  int updates;      // reliable updates done
+  unsigned int counter;  // last-block ticket counter (reset by the last block)
+};
+
+// Geometry of a field: element-major blocks of n1^dim nodes.
+struct Geo {
+  int dim, n1, npe;
+  int n[3];
+  long long ncell, ndof;
+};
+
+// Offsets (in doubles) of the 1D matrices inside the device matrix table;
+// every matrix occupies kMaxN1*kMaxN1 slots, indexed [p*n1 + q].
+enum MatId { kW = 0, kWinv, kPhi0, kPhi1, kM, kRt, kLt, kRb, kLb, kML, kMR, kHR, kHL, kHC, kDn, kNumMats };
+constexpr int kMatStride = kMaxN1 * kMaxN1;
+constexpr int kMatTable = kNumMats * kMatStride;
+
+constexpr int kMaxStates = 8;
+constexpr int kPartialSlots = 4;       // doubles per block in a partials array
+constexpr int kReduceBlocks = 152 * 4; // grid of the vector / reduction kernels
+
+enum StateId { kStP64 = 0, kStP32 = 1, kStV64 = 2, kStV32 = 3, kStMisc = 4 };
+
+constexpr int kProfEvents = 64;  // event pairs per CG batch when profiling
+
+}  // namespace sdg
+
+struct sdg_handle {
+  int device;
+  sdg::Geo g;
+  int dim;
+  double L[3], dx[3];
+  double nu, theta, dt;
+  int precision;
+  double rtol_p, rtol_v;
+  double delta;     // mixed: reliable-update factor
+  int maxit, max_updates;
+  sdg::Basis1D basis;
+
+  // state
+  double* U[3];
+  double* P;
+  // step work
+  double* Vm[3];    // main-grid velocity
+  double* S1[3];    // RK stage 1
+  double* S2[3];    // RK stage 2
+  double* F[3];     // RK3 result Fu
+  double* Vh[3];    // viscous solution U^{n+1/2} on the main grid
+  double* Us[3];    // U* on the dual grids
+  double* b;        // right-hand side
+  double* Pn;       // new pressure
+  double* tmp;      // scratch field
+  // solver vectors
+  // p is double-buffered: the fused apply reads p_old with its halo while
+  // other CTAs write p_new, so the two must not alias.
+  double *r64, *p64[2], *Ap64;
+  float *x32, *r32, *p32[2], *Ap32;
+  sdg::SolverState* st;   // kMaxStates device states
+  sdg::SolverState* st_host;  // pinned mirror
+  double* partials;       // kMaxStates * max_blocks * kPartialSlots
+  long long max_blocks;
+  double* mats;           // device matrix table (kMatTable doubles)
+  cudaEvent_t ev0, ev1, ev2, ev3;
+  // instrumentation
+  long long launches;     // kernels launched by this handle
+  int profile;            // time every fused CG operator launch with events
+  cudaEvent_t pev[2 * sdg::kProfEvents];
+  double prof_ms[2];      // [0] FP64, [1] FP32 fused-apply device time
+  long long prof_n[2];    // launches timed
+};
+
+namespace sdg {
+
+// ---- launchers (sdg_apply_*.cu) -------------------------------------------
+// y = cmass * W x + sum_d s[d] M^{perp d} (H^L x_{i-1} + H^C x_i + H^R x_{i+1})_d
+// If fuse != 0: the input is p = r + beta p_old (beta from `st`, p = r on the
+// first iteration), p is written to p_out, and p^T y is reduced into
+// st->pAp / st->alpha (the CG step-length); the kernel exits at once when
+// st->done is set.
+template <typename T>
+struct ApplyArgs {
+  const T* x;      // input (fuse = 0) or r (fuse = 1)
+  const T* p_old;  // fuse = 1
+  T* p_out;        // fuse = 1
+  T* y;
+  double s[3];
+  double cmass;
+  int fuse;
+  SolverState* st;
+  double* partials;
+};
+
+cudaError_t launch_apply_f64(const sdg_handle* h, const ApplyArgs<double>& a, cudaStream_t s);
+cudaError_t launch_apply_f32(const sdg_handle* h, const ApplyArgs<float>& a, cudaStream_t s);
+
+// per-(dim, n1) dispatch entry points, one per translation unit
+cudaError_t apply_dispatch_2d(const sdg_handle* h, const ApplyArgs<double>& a, cudaStream_t s);
+cudaError_t apply_dispatch_2d(const sdg_handle* h, const ApplyArgs<float>& a, cudaStream_t s);
+cudaError_t apply_dispatch_3d(const sdg_handle* h, const ApplyArgs<double>& a, cudaStream_t s);
+cudaError_t apply_dispatch_3d(const sdg_handle* h, const ApplyArgs<float>& a, cudaStream_t s);
+
+// ---- vector / step kernels (sdg_kernels.cu) --------------------------------
+cudaError_t cg_init_f64(const double* b, const double* Ax, double* r, long long n, SolverState* st,
+                        double* partials, double rtol, int maxit, cudaStream_t s);
+cudaError_t cg_init_f32(const float* b, const float* Ax, float* r, long long n, SolverState* st,
+                        double* partials, double rtol, int maxit, cudaStream_t s);
+cudaError_t cg_update_f64(double* x, double* r, const double* p, const double* Ap, long long n,
+                          SolverState* st, double* partials, cudaStream_t s);
+cudaError_t cg_update_f32(float* x, float* r, const float* p, const float* Ap, long long n,
+                          SolverState* st, double* partials, cudaStream_t s);
+// FP32 CG with FP64 reliable updates:
+//   rel_accumulate: x64 += x32 / sigma, x32 = 0
+//   rel_residual:   r64 = b - Ax (FP64), mean and ||r - mean|| reduced in FP64;
+//                   the last block replaces the recursive residual norm by the
+//                   true one (scaled by sigma^2) and decides convergence.  With
+//                   init = 1 it also starts the solve (sigma = 1/||b||, iter = 0).
+//   rel_convert:    r32 = sigma (r64 - mean)
+cudaError_t rel_accumulate(double* x64, float* x32, long long n, const SolverState* st, cudaStream_t s);
+cudaError_t rel_residual(const double* b, const double* Ax, double* r64, long long n, SolverState* st,
+                         double* partials, double rtol, int maxit, double delta, int init, cudaStream_t s);
+cudaError_t rel_convert(const double* r64, float* r32, long long n, const SolverState* st, cudaStream_t s);
+
+// step stages
+cudaError_t k_dual_to_main(const sdg_handle* h, int d, const double* in, double* out, cudaStream_t s);
+cudaError_t k_main_to_dual(const sdg_handle* h, int d, const double* in, double* out, cudaStream_t s);
+// out_c = a * V0_c + b * (V_c + dt L(V)_c) for every component c
+cudaError_t k_convect_stage(const sdg_handle* h, const double* const* V0, const double* const* V,
+                            double* const* out, double a, double b, cudaStream_t s);
+// b = W F, x0 = F
+cudaError_t k_mass_rhs(const sdg_handle* h, const double* F, double* b, double* x0, cudaStream_t s);
+// out = base + scale * sum_d (1/dx_d) M^{perp d} (Rb U_d - Lb U_d,shift)  ; reduces sum(out) into st->red[0]
+cudaError_t k_divergence(const sdg_handle* h, const double* const* U, const double* base, double scale,
+                         double* out, SolverState* st, double* partials, cudaStream_t s);
+// x -= st->red[slot] * factor
+cudaError_t k_shift(double* x, long long n, const SolverState* st, int slot, double factor, cudaStream_t s);
+cudaError_t k_velocity_update(const sdg_handle* h, const double* const* Ustar, const double* Pn,
+                              const double* Po, double* const* U, cudaStream_t s);
+// st->red[slot] = sum W x (y == NULL) or sum W x y
+cudaError_t k_weighted_sum(const sdg_handle* h, const double* x, const double* y, SolverState* st,
+                           int slot, double* partials, cudaStream_t s);
+// st->red[slot] = sum x*x
+cudaError_t k_norm2(const double* x, long long n, SolverState* st, int slot, double* partials, cudaStream_t s);
+
+}  // namespace sdg

@@ -1,0 +1,551 @@
+// Vector kernels of the CG solvers and the per-node kernels of the time step
+// (L2 projections, Rusanov convection stage, pressure right-hand side,
+// velocity update, reductions).
+#include "sdg_device.cuh"
+
+namespace sdg {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned grid_for(long long n) {
+  long long b = (n + kThreads - 1) / kThreads;
+  if (b > kReduceBlocks) b = kReduceBlocks;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+inline unsigned grid_full(long long n) {
+  long long b = (n + kThreads - 1) / kThreads;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+// ------------------------------------------------------------------ CG vectors
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_cg_init(const T* __restrict__ b, const T* __restrict__ Ax, T* __restrict__ r, long long n,
+              SolverState* st, double* partials, double rtol, int maxit) {
+  double rr = 0.0, bb = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T bi = b[i];
+    const T ri = bi - Ax[i];
+    r[i] = ri;
+    rr += (double)ri * (double)ri;
+    bb += (double)bi * (double)bi;
+  }
+  double v[2] = {rr, bb}, tot[2];
+  if (grid_sum<2>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
+    st->rr = tot[0];
+    st->rr_old = tot[0];
+    st->bnorm2 = tot[1];
+    st->tol2 = rtol * rtol * tot[1];
+    st->iter = 0;
+    st->maxit = maxit;
+    st->status = SDG_OK;
+    st->alpha = 0.0;
+    st->pAp = 0.0;
+    st->reliable = 0;
+    st->pause = 0;
+    st->updates = 0;
+    st->maxrr = tot[0];
+    st->delta2 = 0.0;
+    st->done = (tot[1] == 0.0 || tot[0] <= st->tol2) ? 1 : 0;
+    if (!isfinite(tot[0]) || !isfinite(tot[1])) {
+      st->done = 1;
+      st->status = SDG_ERR_BREAKDOWN;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_cg_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ Ap,
+                long long n, SolverState* st, double* partials) {
+  if (st->done || st->pause) return;
+  const T alpha = (T)st->alpha;
+  double rr = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const T ri = fma(-alpha, Ap[i], r[i]);
+    r[i] = ri;
+    rr += (double)ri * (double)ri;
+  }
+  double v[1] = {rr}, tot[1];
+  if (grid_sum<1>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
+    const double rr = tot[0];
+    st->rr_old = st->rr;
+    st->rr = rr;
+    st->iter += 1;
+    if (rr > st->maxrr) st->maxrr = rr;
+    if (!isfinite(rr)) {
+      st->done = 1;
+      st->status = SDG_ERR_BREAKDOWN;
+    } else if (rr <= st->tol2) {
+      // plain CG stops here; reliable mode confirms with the FP64 residual
+      if (st->reliable) st->pause = 1;
+      else { st->done = 1; st->status = SDG_OK; }
+    } else if (st->reliable && rr < st->delta2 * st->maxrr) {
+      st->pause = 1;
+    } else if (st->iter >= st->maxit) {
+      st->done = 1;
+      st->status = SDG_ERR_NOT_CONVERGED;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ mixed precision
+// x64 += x32 / sigma ; x32 = 0
+__global__ void __launch_bounds__(kThreads)
+    k_rel_accumulate(double* __restrict__ x64, float* __restrict__ x32, long long n, const SolverState* st) {
+  const double inv = 1.0 / st->sigma;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    x64[i] += (double)x32[i] * inv;
+    x32[i] = 0.0f;
+  }
+}
+
+// r = b - Ax in FP64 with sum(r), sum(r^2), sum(b^2).  The last block
+// replaces the recursive residual by the true one (mean removed, scaled by
+// sigma^2) and decides convergence.
+__global__ void __launch_bounds__(kThreads)
+    k_rel_residual(const double* __restrict__ b, const double* __restrict__ Ax, double* __restrict__ r,
+                   long long n, SolverState* st, double* partials, double rtol, int maxit, double delta,
+                   int init) {
+  double s = 0.0, ss = 0.0, bb = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double bi = b[i];
+    const double ri = bi - Ax[i];
+    r[i] = ri;
+    s += ri;
+    ss += ri * ri;
+    bb += bi * bi;
+  }
+  double v[3] = {s, ss, bb}, tot[3];
+  if (grid_sum<3>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
+    const double mean = tot[0] / (double)n;
+    double rrp = tot[1] - (double)n * mean * mean;
+    if (rrp < 0.0) rrp = 0.0;
+    if (init) {
+      st->bnorm2 = tot[2];
+      st->sigma = tot[2] > 0.0 ? 1.0 / sqrt(tot[2]) : 1.0;
+      st->tol2 = rtol * rtol * tot[2] * st->sigma * st->sigma;
+      st->iter = 0;
+      st->maxit = maxit;
+      st->updates = 0;
+      st->reliable = 1;
+      st->delta2 = delta * delta;
+      st->status = SDG_OK;
+      st->alpha = 0.0;
+      st->pAp = 0.0;
+    } else {
+      st->updates += 1;
+    }
+    const double rr = rrp * st->sigma * st->sigma;
+    st->mean = mean;
+    // the next direction uses beta = rr_true / rr_k, rr_k being the residual
+    // norm of the iteration before the one that triggered the update
+    if (init) st->rr_old = rr;
+    st->rr = rr;
+    st->maxrr = rr;
+    st->pause = 0;
+    st->done = (tot[2] == 0.0 || rr <= st->tol2) ? 1 : 0;
+    if (!isfinite(rr)) {
+      st->done = 1;
+      st->status = SDG_ERR_BREAKDOWN;
+    }
+  }
+}
+
+// r32 = sigma (r64 - mean)
+__global__ void __launch_bounds__(kThreads)
+    k_rel_convert(const double* __restrict__ r64, float* __restrict__ r32, long long n, const SolverState* st) {
+  const double mean = st->mean, sigma = st->sigma;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    r32[i] = (float)((r64[i] - mean) * sigma);
+}
+
+// ------------------------------------------------------------------ step stages
+// Per-node kernels: one thread per output node; the 1D matrices are staged
+// in shared memory because the row index varies across the warp.
+struct StepParams {
+  Geo g;
+  double invdx[3];
+};
+
+__device__ __forceinline__ void load_mats(const double* mats, double* s_m, const int* ids, int nid) {
+  for (int k = 0; k < nid; ++k)
+    for (int i = threadIdx.x; i < kMatStride; i += blockDim.x) s_m[k * kMatStride + i] = mats[ids[k] * kMatStride + i];
+  __syncthreads();
+}
+
+// out[e] = M^-1 (M^L in[e-1] + M^R in[e]) along d   (Eq. l2forward)
+// out[e] = M^-1 (M^L in[e] + M^R in[e+1]) along d   (Eq. l2backward)
+template <bool TO_MAIN>
+__global__ void __launch_bounds__(kThreads)
+    k_project(Geo g, int d, const double* __restrict__ in, double* __restrict__ out, const double* mats) {
+  __shared__ double s_m[3 * kMatStride];
+  const int ids[3] = {kML, kMR, kWinv};
+  load_mats(mats, s_m, ids, 3);
+  const double* ML = s_m;
+  const double* MR = s_m + kMatStride;
+  const double* winv = s_m + 2 * kMatStride;
+  const int n1 = g.n1;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.ndof;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int e[3], l[3];
+    split_index(g, idx, e, l);
+    const long long ec = elem_of(g, e);
+    const long long en = elem_shift(g, e, d, TO_MAIN ? -1 : +1);
+    const int m = l[d];
+    int l0[3] = {l[0], l[1], l[2]};
+    l0[d] = 0;
+    const int lb = local_of(g, l0), st = lstride(g, d);
+    const double* a = in + (TO_MAIN ? en : ec) * g.npe + lb;  // multiplied by M^L
+    const double* b = in + (TO_MAIN ? ec : en) * g.npe + lb;  // multiplied by M^R
+    double acc = 0.0;
+    for (int q = 0; q < n1; ++q) acc += ML[m * n1 + q] * a[q * st] + MR[m * n1 + q] * b[q * st];
+    out[idx] = acc * winv[m];
+  }
+}
+
+// Trace of field X of element el at xi = side along d, at the face node given
+// by the other local indices (lb = local base with l_d = 0).
+__device__ __forceinline__ double trace(const double* X, long long el, int npe, int lb, int st, int n1,
+                                        const double* phis) {
+  const double* p = X + el * npe + lb;
+  double s = 0.0;
+  for (int q = 0; q < n1; ++q) s += phis[q] * p[q * st];
+  return s;
+}
+
+// out_c = a V0_c + b (V_c + dt L(V)_c), with the collocated Rusanov DG operator
+//   L(q) = - sum_d (1/dx_d) M_d^-1 [phi(1) F^_{e+1/2} - phi(0) F^_{e-1/2} - Dn^T W (q v_d)]
+// F^ = (q^- v^- + q^+ v^+)/2 - s (q^+ - q^-)/2,  s = 2 max(|v_d^-|, |v_d^+|).
+struct ConvectParams {
+  Geo g;
+  double invdx[3];
+  const double* V0[3];
+  const double* V[3];
+  double* out[3];
+  double a, b, dt;
+};
+
+__global__ void __launch_bounds__(kThreads) k_convect(ConvectParams p, const double* mats) {
+  __shared__ double s_m[5 * kMatStride];
+  const int ids[5] = {kW, kWinv, kPhi0, kPhi1, kDn};
+  load_mats(mats, s_m, ids, 5);
+  const double* w = s_m;
+  const double* winv = s_m + kMatStride;
+  const double* phi0 = s_m + 2 * kMatStride;
+  const double* phi1 = s_m + 3 * kMatStride;
+  const double* Dn = s_m + 4 * kMatStride;
+  const Geo& g = p.g;
+  const int n1 = g.n1, dim = g.dim;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.ndof;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int e[3], l[3];
+    split_index(g, idx, e, l);
+    const long long ec = elem_of(g, e);
+    double Lc[3] = {0.0, 0.0, 0.0};
+    for (int d = 0; d < dim; ++d) {
+      const long long em = elem_shift(g, e, d, -1), ep = elem_shift(g, e, d, +1);
+      const int m = l[d];
+      int l0[3] = {l[0], l[1], l[2]};
+      l0[d] = 0;
+      const int lb = local_of(g, l0), st = lstride(g, d);
+      const double* Vd = p.V[d];
+      // normal velocity traces at the faces e-1/2 and e+1/2
+      const double vd_l_m = trace(Vd, em, g.npe, lb, st, n1, phi1);  // from e-1
+      const double vd_l_p = trace(Vd, ec, g.npe, lb, st, n1, phi0);  // from e
+      const double vd_r_m = trace(Vd, ec, g.npe, lb, st, n1, phi1);  // from e
+      const double vd_r_p = trace(Vd, ep, g.npe, lb, st, n1, phi0);  // from e+1
+      const double s_l = 2.0 * fmax(fabs(vd_l_m), fabs(vd_l_p));
+      const double s_r = 2.0 * fmax(fabs(vd_r_m), fabs(vd_r_p));
+      const double* vdc = Vd + ec * g.npe + lb;
+      for (int c = 0; c < dim; ++c) {
+        const double* Q = p.V[c];
+        const double q_l_m = trace(Q, em, g.npe, lb, st, n1, phi1);
+        const double q_l_p = trace(Q, ec, g.npe, lb, st, n1, phi0);
+        const double q_r_m = trace(Q, ec, g.npe, lb, st, n1, phi1);
+        const double q_r_p = trace(Q, ep, g.npe, lb, st, n1, phi0);
+        const double f_l = 0.5 * (q_l_m * vd_l_m + q_l_p * vd_l_p) - 0.5 * s_l * (q_l_p - q_l_m);
+        const double f_r = 0.5 * (q_r_m * vd_r_m + q_r_p * vd_r_p) - 0.5 * s_r * (q_r_p - q_r_m);
+        const double* qc = Q + ec * g.npe + lb;
+        double vol = 0.0;
+        for (int k = 0; k < n1; ++k) vol += w[k] * Dn[k * n1 + m] * qc[k * st] * vdc[k * st];
+        const double surf = phi1[m] * f_r - phi0[m] * f_l;
+        Lc[c] -= p.invdx[d] * winv[m] * (surf - vol);
+      }
+    }
+    for (int c = 0; c < dim; ++c) {
+      const double v = p.V[c][idx];
+      const double v0 = p.a != 0.0 ? p.V0[c][idx] : 0.0;
+      p.out[c][idx] = p.a * v0 + p.b * (v + p.dt * Lc[c]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_mass(Geo g, const double* __restrict__ F, double* __restrict__ b, double* __restrict__ x0,
+           const double* mats) {
+  __shared__ double s_w[kMaxN1];
+  if (threadIdx.x < kMaxN1) s_w[threadIdx.x] = mats[kW * kMatStride + threadIdx.x];
+  __syncthreads();
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.ndof;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int e[3], l[3];
+    split_index(g, idx, e, l);
+    double W = s_w[l[0]] * s_w[l[1]];
+    if (g.dim == 3) W *= s_w[l[2]];
+    const double f = F[idx];
+    b[idx] = W * f;
+    if (x0) x0[idx] = f;
+  }
+}
+
+// out = base + scale * sum_d (1/dx_d) M^{perp d} (Rb U_d[e] - Lb U_d[e-1])   (Eq. pSDG1)
+struct DivParams {
+  Geo g;
+  double invdx[3];
+  const double* U[3];
+  const double* base;
+  double scale;
+  double* out;
+};
+
+__global__ void __launch_bounds__(kThreads) k_div(DivParams p, const double* mats, SolverState* st,
+                                                  double* partials) {
+  __shared__ double s_m[3 * kMatStride];
+  const int ids[3] = {kRb, kLb, kW};
+  load_mats(mats, s_m, ids, 3);
+  const double* Rb = s_m;
+  const double* Lb = s_m + kMatStride;
+  const double* w = s_m + 2 * kMatStride;
+  const Geo& g = p.g;
+  const int n1 = g.n1;
+  double sum = 0.0;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.ndof;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int e[3], l[3];
+    split_index(g, idx, e, l);
+    const long long ec = elem_of(g, e);
+    double acc = 0.0;
+    for (int d = 0; d < g.dim; ++d) {
+      const long long em = elem_shift(g, e, d, -1);
+      const int m = l[d];
+      int l0[3] = {l[0], l[1], l[2]};
+      l0[d] = 0;
+      const int lb = local_of(g, l0), stp = lstride(g, d);
+      const double* uc = p.U[d] + ec * g.npe + lb;
+      const double* um = p.U[d] + em * g.npe + lb;
+      double t = 0.0;
+      for (int q = 0; q < n1; ++q) t += Rb[m * n1 + q] * uc[q * stp] - Lb[m * n1 + q] * um[q * stp];
+      double wp = 1.0;
+      for (int d2 = 0; d2 < g.dim; ++d2)
+        if (d2 != d) wp *= w[l[d2]];
+      acc += p.invdx[d] * wp * t;
+    }
+    const double v = (p.base ? p.base[idx] : 0.0) + p.scale * acc;
+    p.out[idx] = v;
+    sum += v;
+  }
+  double v1[1] = {sum}, tot[1];
+  if (grid_sum<1>(v1, partials, &st->counter, tot) && threadIdx.x == 0) st->red[0] = tot[0];
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_shift_kernel(double* __restrict__ x, long long n, const SolverState* st, int slot, double factor) {
+  const double c = st->red[slot] * factor;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] -= c;
+}
+
+// U_d = U*_d - (dt/dx_d) M^-1 (R~ q[e+1] - L~ q[e]),  q = theta Pn + (1-theta) Po   (Eq. LOvelocityU)
+struct VelParams {
+  Geo g;
+  double coef[3];  // dt / dx_d
+  double theta;
+  const double* Us[3];
+  const double* Pn;
+  const double* Po;
+  double* U[3];
+};
+
+__global__ void __launch_bounds__(kThreads) k_velocity(VelParams p, const double* mats) {
+  __shared__ double s_m[3 * kMatStride];
+  const int ids[3] = {kRt, kLt, kWinv};
+  load_mats(mats, s_m, ids, 3);
+  const double* Rt = s_m;
+  const double* Lt = s_m + kMatStride;
+  const double* winv = s_m + 2 * kMatStride;
+  const Geo& g = p.g;
+  const int n1 = g.n1;
+  const double th = p.theta, th1 = 1.0 - p.theta;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.ndof;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int e[3], l[3];
+    split_index(g, idx, e, l);
+    const long long ec = elem_of(g, e);
+    for (int d = 0; d < g.dim; ++d) {
+      const long long ep = elem_shift(g, e, d, +1);
+      const int m = l[d];
+      int l0[3] = {l[0], l[1], l[2]};
+      l0[d] = 0;
+      const int lb = local_of(g, l0), stp = lstride(g, d);
+      double t = 0.0;
+      for (int q = 0; q < n1; ++q) {
+        const long long ic = ec * g.npe + lb + q * stp, ip = ep * g.npe + lb + q * stp;
+        const double qc = th * p.Pn[ic] + th1 * p.Po[ic];
+        const double qp = th * p.Pn[ip] + th1 * p.Po[ip];
+        t += Rt[m * n1 + q] * qp - Lt[m * n1 + q] * qc;
+      }
+      p.U[d][idx] = p.Us[d][idx] - p.coef[d] * winv[m] * t;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_wsum(Geo g, const double* __restrict__ x, const double* __restrict__ y, SolverState* st, int slot,
+           double* partials, const double* mats) {
+  __shared__ double s_w[kMaxN1];
+  if (threadIdx.x < kMaxN1) s_w[threadIdx.x] = mats[kW * kMatStride + threadIdx.x];
+  __syncthreads();
+  double sum = 0.0;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.ndof;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int e[3], l[3];
+    split_index(g, idx, e, l);
+    double W = s_w[l[0]] * s_w[l[1]];
+    if (g.dim == 3) W *= s_w[l[2]];
+    sum += W * x[idx] * (y ? y[idx] : 1.0);
+  }
+  double v1[1] = {sum}, tot[1];
+  if (grid_sum<1>(v1, partials, &st->counter, tot) && threadIdx.x == 0) st->red[slot] = tot[0];
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_norm2_kernel(const double* __restrict__ x, long long n, SolverState* st, int slot, double* partials) {
+  double sum = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    sum += x[i] * x[i];
+  double v1[1] = {sum}, tot[1];
+  if (grid_sum<1>(v1, partials, &st->counter, tot) && threadIdx.x == 0) st->red[slot] = tot[0];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+cudaError_t cg_init_f64(const double* b, const double* Ax, double* r, long long n, SolverState* st,
+                        double* partials, double rtol, int maxit, cudaStream_t s) {
+  k_cg_init<double><<<grid_for(n), kThreads, 0, s>>>(b, Ax, r, n, st, partials, rtol, maxit);
+  return cudaGetLastError();
+}
+cudaError_t cg_init_f32(const float* b, const float* Ax, float* r, long long n, SolverState* st,
+                        double* partials, double rtol, int maxit, cudaStream_t s) {
+  k_cg_init<float><<<grid_for(n), kThreads, 0, s>>>(b, Ax, r, n, st, partials, rtol, maxit);
+  return cudaGetLastError();
+}
+cudaError_t cg_update_f64(double* x, double* r, const double* p, const double* Ap, long long n,
+                          SolverState* st, double* partials, cudaStream_t s) {
+  k_cg_update<double><<<grid_for(n), kThreads, 0, s>>>(x, r, p, Ap, n, st, partials);
+  return cudaGetLastError();
+}
+cudaError_t cg_update_f32(float* x, float* r, const float* p, const float* Ap, long long n,
+                          SolverState* st, double* partials, cudaStream_t s) {
+  k_cg_update<float><<<grid_for(n), kThreads, 0, s>>>(x, r, p, Ap, n, st, partials);
+  return cudaGetLastError();
+}
+cudaError_t rel_accumulate(double* x64, float* x32, long long n, const SolverState* st, cudaStream_t s) {
+  k_rel_accumulate<<<grid_for(n), kThreads, 0, s>>>(x64, x32, n, st);
+  return cudaGetLastError();
+}
+cudaError_t rel_residual(const double* b, const double* Ax, double* r64, long long n, SolverState* st,
+                         double* partials, double rtol, int maxit, double delta, int init, cudaStream_t s) {
+  k_rel_residual<<<grid_for(n), kThreads, 0, s>>>(b, Ax, r64, n, st, partials, rtol, maxit, delta, init);
+  return cudaGetLastError();
+}
+cudaError_t rel_convert(const double* r64, float* r32, long long n, const SolverState* st, cudaStream_t s) {
+  k_rel_convert<<<grid_for(n), kThreads, 0, s>>>(r64, r32, n, st);
+  return cudaGetLastError();
+}
+
+cudaError_t k_dual_to_main(const sdg_handle* h, int d, const double* in, double* out, cudaStream_t s) {
+  k_project<true><<<grid_full(h->g.ndof), kThreads, 0, s>>>(h->g, d, in, out, h->mats);
+  return cudaGetLastError();
+}
+cudaError_t k_main_to_dual(const sdg_handle* h, int d, const double* in, double* out, cudaStream_t s) {
+  k_project<false><<<grid_full(h->g.ndof), kThreads, 0, s>>>(h->g, d, in, out, h->mats);
+  return cudaGetLastError();
+}
+cudaError_t k_convect_stage(const sdg_handle* h, const double* const* V0, const double* const* V,
+                            double* const* out, double a, double b, cudaStream_t s) {
+  ConvectParams p;
+  p.g = h->g;
+  for (int d = 0; d < 3; ++d) {
+    p.invdx[d] = d < h->dim ? 1.0 / h->dx[d] : 0.0;
+    p.V0[d] = d < h->dim && V0 ? V0[d] : nullptr;
+    p.V[d] = d < h->dim ? V[d] : nullptr;
+    p.out[d] = d < h->dim ? out[d] : nullptr;
+  }
+  p.a = a;
+  p.b = b;
+  p.dt = h->dt;
+  k_convect<<<grid_full(h->g.ndof), kThreads, 0, s>>>(p, h->mats);
+  return cudaGetLastError();
+}
+cudaError_t k_mass_rhs(const sdg_handle* h, const double* F, double* b, double* x0, cudaStream_t s) {
+  k_mass<<<grid_full(h->g.ndof), kThreads, 0, s>>>(h->g, F, b, x0, h->mats);
+  return cudaGetLastError();
+}
+cudaError_t k_divergence(const sdg_handle* h, const double* const* U, const double* base, double scale,
+                         double* out, SolverState* st, double* partials, cudaStream_t s) {
+  DivParams p;
+  p.g = h->g;
+  for (int d = 0; d < 3; ++d) {
+    p.invdx[d] = d < h->dim ? 1.0 / h->dx[d] : 0.0;
+    p.U[d] = d < h->dim ? U[d] : nullptr;
+  }
+  p.base = base;
+  p.scale = scale;
+  p.out = out;
+  k_div<<<grid_for(h->g.ndof), kThreads, 0, s>>>(p, h->mats, st, partials);
+  return cudaGetLastError();
+}
+cudaError_t k_shift(double* x, long long n, const SolverState* st, int slot, double factor, cudaStream_t s) {
+  k_shift_kernel<<<grid_for(n), kThreads, 0, s>>>(x, n, st, slot, factor);
+  return cudaGetLastError();
+}
+cudaError_t k_velocity_update(const sdg_handle* h, const double* const* Ustar, const double* Pn,
+                              const double* Po, double* const* U, cudaStream_t s) {
+  VelParams p;
+  p.g = h->g;
+  for (int d = 0; d < 3; ++d) {
+    p.coef[d] = d < h->dim ? h->dt / h->dx[d] : 0.0;
+    p.Us[d] = d < h->dim ? Ustar[d] : nullptr;
+    p.U[d] = d < h->dim ? U[d] : nullptr;
+  }
+  p.theta = h->theta;
+  p.Pn = Pn;
+  p.Po = Po;
+  k_velocity<<<grid_full(h->g.ndof), kThreads, 0, s>>>(p, h->mats);
+  return cudaGetLastError();
+}
+cudaError_t k_weighted_sum(const sdg_handle* h, const double* x, const double* y, SolverState* st, int slot,
+                           double* partials, cudaStream_t s) {
+  k_wsum<<<grid_for(h->g.ndof), kThreads, 0, s>>>(h->g, x, y, st, slot, partials, h->mats);
+  return cudaGetLastError();
+}
+cudaError_t k_norm2(const double* x, long long n, SolverState* st, int slot, double* partials, cudaStream_t s) {
+  k_norm2_kernel<<<grid_for(n), kThreads, 0, s>>>(x, n, st, slot, partials);
+  return cudaGetLastError();
+}
+
+}  // namespace sdg

@@ -1,0 +1,329 @@
+"""Parity of the CUDA path (called through the C ABI) with the CPU oracle.
+
+Tolerances (relative L2 over the whole field unless stated):
+  * operator applies, projections, convection, right-hand side, velocity
+    update in FP64: 1e-13 (a handful of roundings per output; random data has
+    no cancellation);
+  * FP32 operator apply: 2e-5 (3 n1 d terms in FP32, unit roundoff 6e-8);
+  * pressure / velocity after each FP64 step: 1e-11; mixed-precision steps:
+    1e-10 (the accuracy the solvers are asked for).
+Grids are chosen to span several element tiles with ragged tails.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import Grid, Oracle, cg  # noqa: E402
+import sdg_inputs as si  # noqa: E402
+from paper_1602_05806_gb300 import sdg  # noqa: E402
+from paper_1602_05806_gb300.workloads import taylor_green_state, workload_state  # noqa: E402
+
+TWO_PI = 2.0 * math.pi
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def make(dim, n, N, nu=0.05, theta=0.6, dt=0.03, L=None):
+    L = L or (TWO_PI,) * dim
+    o = Oracle(Grid(dim, n, L), N, nu, theta, dt)
+    h = sdg.Handle(dim, n, L, N, nu, theta, dt)
+    return o, h
+
+
+APPLY_CASES = ([(2, (11, 7), N) for N in range(0, 12)]
+               + [(2, (1, 5), 3), (2, (2, 2), 7), (2, (37, 3), 1)]
+               + [(3, (5, 3, 4), N) for N in range(0, 7)]
+               + [(3, (3, 2, 3), N) for N in range(7, 12)]
+               + [(3, (1, 2, 3), 4)])
+
+
+@pytest.mark.parametrize("dim,n,N", APPLY_CASES)
+def test_pressure_and_viscous_apply(dim, n, N):
+    o, h = make(dim, n, N, L=(1.3, 2.1, 0.7)[:dim])
+    x = si.random_vector(1000 + N, o.ndof).reshape(o.shape)
+    X = dev(x)
+    Y = torch.empty_like(X)
+    h.pressure_apply(X, Y)
+    assert rel(host(Y), o.pressure_apply(x)) <= 1e-13
+    h.viscous_apply(X, Y)
+    assert rel(host(Y), o.viscous_apply(x)) <= 1e-13
+    # FP32 operator on FP32-rounded input
+    x32 = x.astype(np.float32)
+    X32 = dev(x32, torch.float32)
+    Y32 = torch.empty_like(X32)
+    h.pressure_apply(X32, Y32)
+    assert rel(host(Y32), o.pressure_apply(x32.astype(np.float64))) <= 2e-5
+    h.viscous_apply(X32, Y32)
+    assert rel(host(Y32), o.viscous_apply(x32.astype(np.float64))) <= 2e-5
+
+
+@pytest.mark.parametrize("dim,n,N", [(2, (9, 6), 3), (2, (5, 7), 6), (3, (3, 4, 3), 2)])
+def test_pressure_cg_fp64(dim, n, N):
+    o, h = make(dim, n, N)
+    rng = np.random.default_rng(N)
+    # b in the range of the operator (its kernel is larger than the constants for odd N)
+    b = o.pressure_apply(rng.standard_normal(o.shape))
+    x0 = rng.standard_normal(o.shape)
+    ref = cg(o.pressure_apply, b, x0, 1e-14)
+    h.set_options(sdg.SDG_FP64, 1e-14, 1e-14, 1000000)
+    B, X = dev(b), dev(x0)
+    info = h.pressure_cg(B, X)
+    assert info["status"] == sdg.SDG_OK
+    assert abs(info["iters"] - ref.iters) <= max(2, 0.03 * ref.iters)
+    assert rel(host(X), ref.x) <= 1e-11
+    # true residual of the GPU solution with the oracle operator
+    xg = host(X)
+    assert np.linalg.norm(b - o.pressure_apply(xg)) <= 1e-12 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("dim,n,N", [(2, (9, 6), 3), (2, (6, 6), 5), (3, (3, 3, 4), 2)])
+def test_pressure_cg_mixed(dim, n, N):
+    o, h = make(dim, n, N)
+    rng = np.random.default_rng(10 + N)
+    b = o.pressure_apply(rng.standard_normal(o.shape))
+    x0 = rng.standard_normal(o.shape)
+    ref = cg(o.pressure_apply, b, x0, 1e-14)
+    h.set_options(sdg.SDG_MIXED, 1e-12, 1e-12, 1000000)
+    h.set_mixed_options(0.1, 1000)
+    B, X = dev(b), dev(x0)
+    info = h.pressure_cg(B, X)
+    assert info["status"] == sdg.SDG_OK, info
+    assert info["outer_iters"] >= 1 and info["applies_fp32"] > 0
+    xg = host(X)
+    assert np.linalg.norm(b - o.pressure_apply(xg)) <= 1e-12 * np.linalg.norm(b) * 1.0001
+    assert rel(xg, ref.x) <= 1e-10
+
+
+def test_viscous_cg_fp64_and_mixed():
+    o, h = make(2, (7, 9), 4, nu=0.3)
+    rng = np.random.default_rng(3)
+    b = rng.standard_normal(o.shape)
+    x0 = rng.standard_normal(o.shape)
+    ref = cg(o.viscous_apply, b, x0, 1e-14)
+    h.set_options(sdg.SDG_FP64, 1e-14, 1e-14, 1000000)
+    X = dev(x0)
+    info = h.viscous_cg(dev(b), X)
+    assert info["status"] == sdg.SDG_OK
+    assert rel(host(X), ref.x) <= 1e-12
+    h.set_options(sdg.SDG_MIXED, 1e-12, 1e-12, 1000000)
+    X = dev(x0)
+    info = h.viscous_cg(dev(b), X)
+    assert info["status"] == sdg.SDG_OK and info["applies_fp32"] > 0
+    assert rel(host(X), ref.x) <= 1e-11
+
+
+def test_cg_zero_rhs_and_maxit():
+    o, h = make(2, (4, 4), 2)
+    x0 = np.random.default_rng(1).standard_normal(o.shape)
+    X = dev(x0)
+    info = h.pressure_cg(dev(np.zeros(o.shape)), X)
+    assert info["status"] == sdg.SDG_OK and info["iters"] == 0
+    assert np.array_equal(host(X), x0)
+    # iteration cap reports NOT_CONVERGED and keeps the last iterate
+    b = o.pressure_apply(np.random.default_rng(2).standard_normal(o.shape))
+    h.set_options(sdg.SDG_FP64, 1e-14, 1e-14, 3)
+    X = dev(x0)
+    info = h.pressure_cg(dev(b), X, ok=(sdg.SDG_OK, sdg.SDG_ERR_NOT_CONVERGED))
+    assert info["status"] == sdg.SDG_ERR_NOT_CONVERGED and info["iters"] == 3
+    ref = cg(o.pressure_apply, b, x0, 1e-30, maxit=3)
+    assert rel(host(X), ref.x) <= 1e-12
+
+
+def test_cg_nan_rhs_is_breakdown():
+    o, h = make(2, (4, 4), 2)
+    b = np.zeros(o.shape)
+    b[0, 0, 0, 0] = np.nan
+    info = h.pressure_cg(dev(b), dev(np.zeros(o.shape)), ok=(sdg.SDG_ERR_BREAKDOWN,))
+    assert info["status"] == sdg.SDG_ERR_BREAKDOWN
+
+
+def test_invalid_arguments():
+    with pytest.raises(sdg.SDGError) as e:
+        sdg.Handle(2, (4, 4), (1.0, 1.0), 12, 0.1, 0.5, 0.01)
+    assert e.value.status == sdg.SDG_ERR_INVALID_ARG
+    with pytest.raises(sdg.SDGError):
+        sdg.Handle(2, (4, 4), (1.0, 1.0), 3, 0.1, 0.4, 0.01)
+    with pytest.raises(sdg.SDGError):
+        sdg.Handle(4, (4, 4, 4), (1.0, 1.0, 1.0), 3, 0.1, 0.5, 0.01)
+
+
+# ------------------------------------------------------------------ step stages
+@pytest.mark.parametrize("dim,n,N", [(2, (11, 7), 3), (2, (6, 13), 7), (3, (5, 3, 4), 2), (3, (3, 4, 3), 4)])
+def test_stages(dim, n, N):
+    o, h = make(dim, n, N, nu=0.02, theta=0.55, dt=0.01, L=(1.0, 1.7, 1.3)[:dim])
+    rng = np.random.default_rng(77)
+    fields = [rng.standard_normal(o.shape) for _ in range(dim)]
+    D = [dev(f) for f in fields]
+    out = [torch.empty_like(D[0]) for _ in range(dim)]
+    for d in range(dim):
+        h.dual_to_main(d, D[d], out[d])
+        assert rel(host(out[d]), o.dual_to_main(fields[d], d)) <= 1e-13
+        h.main_to_dual(d, D[d], out[d])
+        assert rel(host(out[d]), o.main_to_dual(fields[d], d)) <= 1e-13
+    # one RK3 convection step of a smooth-ish field
+    V = [0.3 * f for f in fields]
+    h.convect([dev(v) for v in V], out)
+    ref = o.rk3(V)
+    for c in range(dim):
+        assert rel(host(out[c]), ref[c]) <= 1e-13
+    # pressure right-hand side and velocity update
+    P = rng.standard_normal(o.shape)
+    b = torch.empty_like(D[0])
+    h.pressure_rhs(D, dev(P), b)
+    bref = o.pressure_rhs(fields, P)
+    bref = bref - bref.mean()
+    assert rel(host(b), bref) <= 1e-13
+    Pn = rng.standard_normal(o.shape)
+    h.velocity_update(D, dev(Pn), dev(P), out)
+    q = o.theta * Pn + (1 - o.theta) * P
+    uref = o.velocity_update(fields, q)
+    for d in range(dim):
+        assert rel(host(out[d]), uref[d]) <= 1e-13
+
+
+# ------------------------------------------------------------------ full steps
+def _oracle_tg(o, modes=None):
+    U = []
+    if o.dim == 2:
+        for d in range(2):
+            x, y = o.coords(d)
+            v = si.taylor_green_2d(x, y)[d]
+            if modes is not None:
+                v = v + si.perturbation_velocity(modes, x, y)[d]
+            U.append(v)
+        x, y = o.coords(None)
+        P = si.taylor_green_2d(x, y)[2]
+    else:
+        for d in range(3):
+            U.append(si.taylor_green_3d(*o.coords(d))[d])
+        P = si.taylor_green_3d(*o.coords(None))[3]
+    return U, P
+
+
+@pytest.mark.parametrize("precision", [sdg.SDG_FP64, sdg.SDG_MIXED])
+def test_step_parity_tg2d_8x8_N3(precision):
+    """Taylor-Green 8x8, N=3, nu=0.1, theta=0.51, dt=0.01: ten steps, U and P
+    compared with the oracle after every step."""
+    o, h = make(2, (8, 8), 3, nu=0.1, theta=0.51, dt=0.01)
+    o.rtol_p = o.rtol_v = 1e-13
+    h.set_options(precision, 1e-13, 1e-13, 1000000)
+    U, P = _oracle_tg(o)
+    Ug, Pg = taylor_green_state(2, (8, 8), (TWO_PI, TWO_PI), 3)
+    h.set_state([dev(u) for u in Ug], dev(Pg))
+    tol = 1e-11 if precision == sdg.SDG_FP64 else 1e-10
+    Uo = [torch.empty(o.shape, dtype=torch.float64, device="cuda") for _ in range(2)]
+    Po = torch.empty(o.shape, dtype=torch.float64, device="cuda")
+    for step in range(10):
+        U, P, info = o.step(U, P)
+        ginfo = h.step(1)
+        assert ginfo["status"] == sdg.SDG_OK
+        h.get_state(Uo, Po)
+        for d in range(2):
+            assert rel(host(Uo[d]), U[d]) <= tol, (step, d)
+        assert rel(host(Po), P) <= tol, step
+    ke, div = h.diagnostics()
+    assert abs(ke - o.kinetic_energy(U)) <= 1e-12
+    assert div <= 1e-10
+
+
+@pytest.mark.parametrize("precision", [sdg.SDG_FP64, sdg.SDG_MIXED])
+def test_step_parity_3d_ragged(precision):
+    o, h = make(3, (5, 3, 4), 2, nu=0.02, theta=0.6, dt=0.02)
+    o.rtol_p = o.rtol_v = 1e-13
+    h.set_options(precision, 1e-13, 1e-13, 1000000)
+    U, P = _oracle_tg(o)
+    Ug, Pg = taylor_green_state(3, (5, 3, 4), (TWO_PI,) * 3, 2)
+    h.set_state([dev(u) for u in Ug], dev(Pg))
+    tol = 1e-11 if precision == sdg.SDG_FP64 else 1e-10
+    Uo = [torch.empty(o.shape, dtype=torch.float64, device="cuda") for _ in range(3)]
+    Po = torch.empty(o.shape, dtype=torch.float64, device="cuda")
+    for step in range(3):
+        U, P, _ = o.step(U, P)
+        assert h.step(1)["status"] == sdg.SDG_OK
+        h.get_state(Uo, Po)
+        for d in range(3):
+            assert rel(host(Uo[d]), U[d]) <= tol
+        assert rel(host(Po), P) <= tol
+
+
+def test_step_parity_perturbed_64x64_N5_reduced():
+    """The 64x64, N=5 perturbed workload on a 12x10 grid (same degree,
+    viscosity, time step and perturbation), three steps."""
+    w, Ug, Pg = workload_state("tg2d_64x64_N5", n_override=(12, 10))
+    o, h = make(2, w["n"], w["N"], nu=w["nu"], theta=w["theta"], dt=w["dt"])
+    o.rtol_p = o.rtol_v = 1e-13
+    h.set_options(sdg.SDG_FP64, 1e-13, 1e-13, 1000000)
+    m = w["modes"]
+    U, P = _oracle_tg(o, si.stream_modes(m["seed"], m["nmodes"], m["kmax"], m["amplitude"]))
+    h.set_state([dev(u) for u in Ug], dev(Pg))
+    Uo = [torch.empty(o.shape, dtype=torch.float64, device="cuda") for _ in range(2)]
+    Po = torch.empty(o.shape, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        U, P, _ = o.step(U, P)
+        assert h.step(1)["status"] == sdg.SDG_OK
+    h.get_state(Uo, Po)
+    for d in range(2):
+        assert rel(host(Uo[d]), U[d]) <= 1e-11
+    assert rel(host(Po), P) <= 1e-11
+
+
+# ------------------------------------------------------------------ full size (256^2, N=7)
+def test_full_size_apply_256x256_N7():
+    """Every output of the operator at the benchmark size (4.19 M DOF)."""
+    o, h = make(2, (256, 256), 7, nu=1e-3, theta=0.51, dt=2e-3)
+    x = si.random_vector(5, o.ndof).reshape(o.shape)
+    X = dev(x)
+    Y = torch.empty_like(X)
+    h.pressure_apply(X, Y)
+    assert rel(host(Y), o.pressure_apply(x)) <= 1e-13
+    X32 = X.float()
+    Y32 = torch.empty_like(X32)
+    h.pressure_apply(X32, Y32)
+    assert rel(host(Y32), o.pressure_apply(host(X32))) <= 2e-5
+
+
+@pytest.mark.parametrize("precision", [sdg.SDG_FP64, sdg.SDG_MIXED])
+def test_full_size_step_256x256_N7(precision):
+    """One step of the benchmark workload.  The oracle builds its own
+    right-hand side b from the same initial data; the GPU pressure must
+    satisfy theta A' P = b (oracle operator) to 1e-10 and the GPU velocity
+    must be discretely divergence-free."""
+    w, Ug, Pg = workload_state("tg2d_256x256_N7")
+    o, h = make(2, w["n"], w["N"], nu=w["nu"], theta=w["theta"], dt=w["dt"])
+    h.set_options(precision, 1e-12, 1e-12, 1000000)
+    h.set_state([dev(u) for u in Ug], dev(Pg))
+    info = h.step(1)
+    assert info["status"] == sdg.SDG_OK
+    Uo = [torch.empty(o.shape, dtype=torch.float64, device="cuda") for _ in range(2)]
+    Po = torch.empty(o.shape, dtype=torch.float64, device="cuda")
+    h.get_state(Uo, Po)
+    # oracle side: its own initial data and right-hand side
+    m = w["modes"]
+    U, P = _oracle_tg(o, si.stream_modes(m["seed"], m["nmodes"], m["kmax"], m["amplitude"]))
+    V = [o.dual_to_main(U[d], d) for d in range(2)]
+    F = o.rk3(V)
+    Vh = [cg(o.viscous_apply, o.mass_all(F[c]), F[c], 1e-13).x for c in range(2)]
+    Us = [o.main_to_dual(Vh[d], d) for d in range(2)]
+    b = o.pressure_rhs(Us, P)
+    b = b - b.mean()
+    Pgpu = host(Po)
+    assert np.linalg.norm(o.pressure_apply(Pgpu) - b) <= 1e-10 * np.linalg.norm(b)
+    Ugpu = [host(u) for u in Uo]
+    assert np.linalg.norm(o.divergence(Ugpu)) <= 1e-9 * np.linalg.norm(o.divergence(Us))
+    assert abs(o.physical_mean(Pgpu)) <= 1e-12
