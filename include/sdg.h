@@ -89,6 +89,15 @@ int sdg_nodes(int N, double* xi, double* w);
  * (after Eq. pSyst).  `out` holds 10*(N+1)^2 doubles.  Errors: INVALID_ARG. */
 int sdg_matrices(int N, double* out);
 
+/* Orthogonal projector (row-major (N+1)x(N+1), host array `proj`) onto the
+ * local patterns c with (R~ - L~) c = 0, and its dimension (host int, may be
+ * NULL).  Repeated in every cell and multiplied over the directions, these
+ * patterns span the kernel of the periodic pressure operator: the weak
+ * solutions of grad p = 0 of Sec. 2.1 (the constants for even N; the
+ * constants and one per-cell sawtooth-like pattern per direction for odd N).
+ * Errors: INVALID_ARG. */
+int sdg_kernel_projector(int N, double* proj, int* dim);
+
 /* Create a problem: grid, degree N, viscosity nu >= 0, implicitness
  * theta in [1/2, 1] (Sec. 2.1, P^{n+theta}), time step dt > 0.  Allocates
  * the state (U_d, P) and every work buffer on the current CUDA device.
@@ -144,8 +153,10 @@ int sdg_viscous_apply(sdg_handle* h, const void* x, void* y, int fp32,
 
 /* Solve theta A' x = b (Eq. pSyst) by matrix-free CG without
  * preconditioner (Sec. 2.1), in the handle's precision mode.  b: device,
- * sdg_ndof doubles, must be orthogonal to the constants (the periodic kernel;
- * the solve does not project it).  x: device, in = x0, out = solution.
+ * sdg_ndof doubles, must be orthogonal to the kernel of the operator (see
+ * sdg_kernel_projector; the solve does not project it).  x: device, in = x0,
+ * out = solution; its kernel component stays that of x0 (in mixed mode it
+ * is restored explicitly after the FP32 iterations).
  * info may be NULL.  Returns the solve status (OK, NOT_CONVERGED, BREAKDOWN)
  * or INVALID_ARG / CUDA. */
 int sdg_pressure_cg(sdg_handle* h, const double* b, double* x,

@@ -73,6 +73,8 @@ cudaError_t launch_apply_f32(const sdg_handle* h, const ApplyArgs<float>& a, cud
 
 }  // namespace sdg
 
+extern "C" const char* sdg_strerror(int status);
+
 namespace {
 
 template <typename T>
@@ -105,7 +107,11 @@ int cg_loop(sdg_handle* h, const Op& op, T* x, T* r, T* const* p, T* Ap, int sid
   SolverState* st = st_dev(h, sid);
   double* pa = parts(h, sid);
   const long long n = h->g.ndof;
-  long long launched = *launched_io;
+  // direction buffers alternate with the executed iteration: iteration j reads
+  // p[j & 1] and writes p[(j + 1) & 1]; launches skipped after a pause or
+  // convergence do not count, so j restarts from the device iteration count
+  long long launched = h->st_host[sid].iter;
+  (void)launched_io;
   int batch = 4;
   const int pk = sizeof(T) == 8 ? 0 : 1;
   int iter_before = h->st_host[sid].iter;
@@ -149,14 +155,19 @@ int cg_loop(sdg_handle* h, const Op& op, T* x, T* r, T* const* p, T* Ap, int sid
       }
     }
     iter_before = hs.iter;
+    launched = hs.iter;
     if (hs.done || hs.pause) break;
     if (batch < 32) batch *= 2;
   }
-  *launched_io = launched;
   return SDG_OK;
 }
 
 void fill_info(sdg_cg_info* info, const SolverState& hs, int outer, int a64, int a32, int status) {
+  if (status != SDG_OK) {
+    std::snprintf(g_err, sizeof(g_err),
+                  "%s: iter %d, rr %.3e, rr_old %.3e, pAp %.3e, tol2 %.3e, updates %d, reliable %d",
+                  sdg_strerror(status), hs.iter, hs.rr, hs.rr_old, hs.pAp, hs.tol2, hs.updates, hs.reliable);
+  }
   if (!info) return;
   info->iters = hs.iter;
   info->outer_iters = outer;
@@ -190,8 +201,9 @@ int solve_fp64(sdg_handle* h, const Op& op, const double* b, double* x, double r
 // in FP64 and replaces the FP32 one.  Converged when the true residual
 // satisfies ||b - A x|| <= rtol ||b||.
 int solve_mixed(sdg_handle* h, const Op& op, const double* b, double* x, double rtol, int sid,
-                sdg_cg_info* info, cudaStream_t s) {
+                sdg_cg_info* info, cudaStream_t s, bool singular) {
   const long long n = h->g.ndof;
+  if (singular) SDG_CK(cudaMemcpyAsync(h->x0buf, x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   SolverState* st = st_dev(h, sid);
   double* pa = parts(h, sid);
   const double delta = h->delta;
@@ -201,7 +213,7 @@ int solve_mixed(sdg_handle* h, const Op& op, const double* b, double* x, double 
   SDG_CK(cudaMemsetAsync(h->x32, 0, n * sizeof(float), s));
   SDG_K(apply_plain<double>(h, op, x, h->Ap64, s));
   ++a64;
-  SDG_K(rel_residual(b, h->Ap64, h->r64, n, st, pa, rtol, h->maxit, delta, 1, s));
+  SDG_K(rel_residual(b, h->Ap64, h->r64, n, st, pa, rtol, h->maxit, delta, 1, singular, s));
   SDG_K(rel_convert(h->r64, h->r32, n, st, s));
   h->st_host[sid].iter = 0;
   int status = SDG_OK;
@@ -217,7 +229,7 @@ int solve_mixed(sdg_handle* h, const Op& op, const double* b, double* x, double 
     SDG_K(rel_accumulate(x, h->x32, n, st, s));
     SDG_K(apply_plain<double>(h, op, x, h->Ap64, s));
     ++a64;
-    SDG_K(rel_residual(b, h->Ap64, h->r64, n, st, pa, rtol, h->maxit, delta, 0, s));
+    SDG_K(rel_residual(b, h->Ap64, h->r64, n, st, pa, rtol, h->maxit, delta, 0, singular, s));
     ++updates;
     if (hs.done || updates >= h->max_updates) {
       // the FP32 iteration hit maxit or broke down, or the update cap is
@@ -231,6 +243,15 @@ int solve_mixed(sdg_handle* h, const Op& op, const double* b, double* x, double 
     }
     SDG_K(rel_convert(h->r64, h->r32, n, st, s));
   }
+  // CG in exact arithmetic never changes the kernel component of x (every
+  // update lies in the range of the operator); FP32 rounding does, so put it
+  // back to that of x0 (Sec. 2.1: P is defined up to weak solutions of
+  // grad p = 0, and the FP64 solve keeps them fixed).
+  if (singular) {
+    int nl = 0;
+    SDG_CK(kernel_restore(h, x, h->x0buf, s, &nl));
+    h->launches += nl;
+  }
   const SolverState& hs = h->st_host[sid];
   if (status == SDG_OK) status = hs.status;
   fill_info(info, hs, updates, a64, hs.iter, status);
@@ -240,7 +261,8 @@ int solve_mixed(sdg_handle* h, const Op& op, const double* b, double* x, double 
 int solve(sdg_handle* h, bool pressure, const double* b, double* x, sdg_cg_info* info, cudaStream_t s) {
   const Op op = pressure ? pressure_op(h) : viscous_op(h);
   const double rtol = pressure ? h->rtol_p : h->rtol_v;
-  if (h->precision == SDG_MIXED) return solve_mixed(h, op, b, x, rtol, pressure ? kStP32 : kStV32, info, s);
+  if (h->precision == SDG_MIXED)
+    return solve_mixed(h, op, b, x, rtol, pressure ? kStP32 : kStV32, info, s, pressure);
   return solve_fp64(h, op, b, x, rtol, pressure ? kStP64 : kStV64, info, s);
 }
 
@@ -303,6 +325,16 @@ int sdg_matrices(int N, double* out) {
   return SDG_OK;
 }
 
+int sdg_kernel_projector(int N, double* proj, int* dim) {
+  SDG_ARG(N >= 0 && N <= kMaxN, "N must be in [0, 11]");
+  SDG_ARG(proj, "NULL output");
+  Basis1D b;
+  build_basis(N, &b);
+  const int d = kernel_projector(b, proj);
+  if (dim) *dim = d;
+  return SDG_OK;
+}
+
 int sdg_create(const sdg_grid* grid, int N, double nu, double theta, double dt, sdg_handle** out) {
   SDG_ARG(grid && out, "NULL argument");
   SDG_ARG(grid->dim == 2 || grid->dim == 3, "dim must be 2 or 3");
@@ -357,6 +389,10 @@ int sdg_create(const sdg_grid* grid, int N, double nu, double theta, double dt, 
   A_(h->st, kMaxStates);
   A_(h->partials, (size_t)kMaxStates * h->max_blocks * kPartialSlots);
   A_(h->mats, kMatTable);
+  A_(h->x0buf, n);
+  A_(h->kpart, (size_t)kKernelBlocks * h->g.npe);
+  A_(h->kcorr, h->g.npe);
+  A_(h->kproj, h->g.n1 * h->g.n1);
 #undef A_
   if (rc != SDG_OK) { sdg_destroy(h); return rc; }
   if (cudaMallocHost(&h->st_host, kMaxStates * sizeof(SolverState)) != cudaSuccess) {
@@ -379,6 +415,11 @@ int sdg_create(const sdg_grid* grid, int N, double nu, double theta, double dt, 
   const int ids[] = {kM, kRt, kLt, kRb, kLb, kML, kMR, kHR, kHL, kHC, kDn};
   for (int k = 0; k < 11; ++k) std::memcpy(table + ids[k] * kMatStride, mats[k], n1 * n1 * sizeof(double));
   cudaError_t e = cudaMemcpy(h->mats, table, sizeof(table), cudaMemcpyHostToDevice);
+  {
+    double proj[kMaxN1 * kMaxN1];
+    h->kdim = kernel_projector(h->basis, proj);
+    if (e == cudaSuccess) e = cudaMemcpy(h->kproj, proj, n1 * n1 * sizeof(double), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaMemset(h->st, 0, kMaxStates * sizeof(SolverState));
   for (int d = 0; d < h->dim && e == cudaSuccess; ++d) e = cudaMemset(h->U[d], 0, n * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(h->P, 0, n * sizeof(double));
@@ -409,6 +450,7 @@ int sdg_destroy(sdg_handle* h) {
   cudaFree(h->r64); cudaFree(h->p64[0]); cudaFree(h->p64[1]); cudaFree(h->Ap64);
   cudaFree(h->x32); cudaFree(h->r32); cudaFree(h->p32[0]); cudaFree(h->p32[1]); cudaFree(h->Ap32);
   cudaFree(h->st); cudaFree(h->partials); cudaFree(h->mats);
+  cudaFree(h->x0buf); cudaFree(h->kpart); cudaFree(h->kcorr); cudaFree(h->kproj);
   if (h->st_host) cudaFreeHost(h->st_host);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);

@@ -39,9 +39,14 @@ struct Tile {
   static constexpr int NSLOT = TE + 2 * TY * TZ + 2 * TX * TZ + (DIM == 3 ? 2 * TX * TY : 0);
 };
 
+// Stored 1D blocks in the compute precision: H^C symmetric and H^L equal to
+// (H^R)^T exactly, so the stored operator is exactly symmetric; rho[m] is the
+// row sum of the stored [H^L H^C H^R] (zero in exact arithmetic, a few ulps
+// after rounding).
 template <typename T, int N1>
 struct Coef {
   T HL[N1 * N1], HC[N1 * N1], HR[N1 * N1];
+  T rho[N1];
 };
 
 template <typename T, int DIM, int N1>
@@ -227,6 +232,22 @@ __global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
         xc[k] = s_in[sc * NPE + base + k * stride];
         xr[k] = s_in[sr * NPE + base + k * stride];
       }
+      // Every row of [H^L H^C H^R] sums to zero (the operator annihilates
+      // constants), so a line-wide constant c may be removed before the
+      // contractions.  Subtracting the centre node value shrinks the
+      // operands of smooth fields to their local variation and cuts the
+      // rounding error of the product on smooth modes by orders of magnitude
+      // (it matters in FP32).  The stored blocks' row sums rho are not exactly
+      // zero, so the term rho_m (c - x_m) is added back: the result is
+      // (A - diag(rho)) x, an exactly symmetric operator that annihilates
+      // the constants, whatever c is.
+      const T cref = xc[N1 / 2];
+#pragma unroll
+      for (int k = 0; k < N1; ++k) {
+        xl[k] -= cref;
+        xc[k] -= cref;
+        xr[k] -= cref;
+      }
       const T f = a.s[d] * wp;
       T* out = s_out + te * NPE + base;
 #pragma unroll
@@ -238,9 +259,10 @@ __global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
           acc = fma(a.c.HC[m * N1 + k], xc[k], acc);
           acc = fma(a.c.HR[m * N1 + k], xr[k], acc);
         }
+        acc = fma(-a.c.rho[m], xc[m], acc);
         T val = f * acc;
         if (d == 0) {
-          val = fma(a.cmass * wp * s_w[m], xc[m], val);
+          val = fma(a.cmass * wp * s_w[m], xc[m] + cref, val);
           out[m * stride] = val;
         } else {
           out[m * stride] += val;
@@ -291,10 +313,17 @@ cudaError_t launch_apply_t(const sdg_handle* h, const ApplyArgs<T>& in, cudaStre
   using TS = Tile<DIM, N1>;
   ApplyParams<T, DIM, N1> p;
   const Basis1D& b = h->basis;
-  for (int i = 0; i < N1 * N1; ++i) {
-    p.c.HL[i] = (T)b.HL[i];
-    p.c.HC[i] = (T)b.HC[i];
-    p.c.HR[i] = (T)b.HR[i];
+  for (int m = 0; m < N1; ++m)
+    for (int k = 0; k < N1; ++k) {
+      p.c.HR[m * N1 + k] = (T)b.HR[m * N1 + k];
+      p.c.HL[m * N1 + k] = (T)b.HR[k * N1 + m];  // H^L = (H^R)^T
+      p.c.HC[m * N1 + k] = (T)(0.5 * (b.HC[m * N1 + k] + b.HC[k * N1 + m]));
+    }
+  for (int m = 0; m < N1; ++m) {
+    long double rs = 0.0L;
+    for (int k = 0; k < N1; ++k)
+      rs += (long double)p.c.HL[m * N1 + k] + (long double)p.c.HC[m * N1 + k] + (long double)p.c.HR[m * N1 + k];
+    p.c.rho[m] = (T)rs;
   }
   for (int i = 0; i < N1; ++i) p.w[i] = (T)b.w[i];
   p.x = in.x;

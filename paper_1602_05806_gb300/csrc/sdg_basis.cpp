@@ -187,4 +187,74 @@ int build_basis(int N, Basis1D* b) {
   return 0;
 }
 
+namespace {
+
+// Cyclic Jacobi eigen-decomposition of a symmetric n x n matrix A (row-major,
+// destroyed); eigenvalues to lam[], eigenvectors to the columns of V.
+void jacobi_eig(int n, double* A, double* lam, double* V) {
+  for (int i = 0; i < n * n; ++i) V[i] = 0.0;
+  for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) off += A[p * n + q] * A[p * n + q];
+    if (off < 1e-300) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[p * n + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        const double app = A[p * n + p], aqq = A[q * n + q];
+        const double tau = (aqq - app) / (2.0 * apq);
+        const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), sn = t * c;
+        for (int k = 0; k < n; ++k) {  // A <- A J (columns p, q)
+          const double akp = A[k * n + p], akq = A[k * n + q];
+          A[k * n + p] = c * akp - sn * akq;
+          A[k * n + q] = sn * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {  // A <- J^T A (rows p, q)
+          const double apk = A[p * n + k], aqk = A[q * n + k];
+          A[p * n + k] = c * apk - sn * aqk;
+          A[q * n + k] = sn * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double vkp = V[k * n + p], vkq = V[k * n + q];
+          V[k * n + p] = c * vkp - sn * vkq;
+          V[k * n + q] = sn * vkp + c * vkq;
+        }
+      }
+  }
+  for (int i = 0; i < n; ++i) lam[i] = A[i * n + i];
+}
+
+}  // namespace
+
+int kernel_projector(const Basis1D& b, double* proj) {
+  const int n = b.n1;
+  std::vector<double> G(n * n), A(n * n), V(n * n), lam(n);
+  double scale = 0.0;  // size of R~ and L~ (R~ - L~ itself vanishes for N = 1)
+  for (int i = 0; i < n * n; ++i) {
+    G[i] = b.Rt[i] - b.Lt[i];
+    scale = std::fmax(scale, std::fabs(b.Rt[i]) + std::fabs(b.Lt[i]));
+  }
+  scale *= scale;
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < n; ++q) {
+      double s = 0.0;
+      for (int k = 0; k < n; ++k) s += G[k * n + p] * G[k * n + q];
+      A[p * n + q] = s;
+    }
+  jacobi_eig(n, A.data(), lam.data(), V.data());
+  for (int i = 0; i < n * n; ++i) proj[i] = 0.0;
+  int dim = 0;
+  const double tol = 1e-12 * (scale > 0 ? scale : 1.0);
+  for (int j = 0; j < n; ++j) {
+    if (std::fabs(lam[j]) > tol) continue;
+    ++dim;
+    for (int p = 0; p < n; ++p)
+      for (int q = 0; q < n; ++q) proj[p * n + q] += V[p * n + j] * V[q * n + j];
+  }
+  return dim;
+}
+
 }  // namespace sdg

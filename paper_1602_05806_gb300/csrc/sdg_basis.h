@@ -26,4 +26,11 @@ void gauss_legendre(int n, double* xi, double* w);
 // Fill every matrix of degree N (0 <= N <= kMaxN).  Returns 0 or -1.
 int build_basis(int N, Basis1D* b);
 
+// Orthogonal projector (n1 x n1, row-major) onto the kernel of R~ - L~, the
+// local patterns whose weak gradient vanishes when repeated in every cell;
+// the kernel of the periodic pressure operator is the tensor product of this
+// space over the directions, repeated in every element.  Returns its
+// dimension (1 for even N: the constants; 2 for odd N).
+int kernel_projector(const Basis1D& b, double* proj);
+
 }  // namespace sdg

@@ -50,8 +50,9 @@ constexpr int kMatStride = kMaxN1 * kMaxN1;
 constexpr int kMatTable = kNumMats * kMatStride;
 
 constexpr int kMaxStates = 8;
+constexpr int kKernelBlocks = 512;     // grid of the per-local-node element sum
 constexpr int kPartialSlots = 4;       // doubles per block in a partials array
-constexpr int kReduceBlocks = 152 * 4; // grid of the vector / reduction kernels
+constexpr int kReduceBlocks = 152 * 8; // grid of the vector / reduction kernels
 
 enum StateId { kStP64 = 0, kStP32 = 1, kStV64 = 2, kStV32 = 3, kStMisc = 4 };
 
@@ -94,6 +95,12 @@ struct sdg_handle {
   double* partials;       // kMaxStates * max_blocks * kPartialSlots
   long long max_blocks;
   double* mats;           // device matrix table (kMatTable doubles)
+  // kernel restoration of mixed pressure solves (see kernel_projector)
+  double* x0buf;          // copy of x0 (ndof)
+  double* kpart;          // per-block partial element sums (kKernelBlocks * npe)
+  double* kcorr;          // correction pattern (npe)
+  double* kproj;          // 1D kernel projector (n1 * n1)
+  int kdim;               // dimension of the 1D kernel
   cudaEvent_t ev0, ev1, ev2, ev3;
   // instrumentation
   long long launches;     // kernels launched by this handle
@@ -148,11 +155,18 @@ cudaError_t cg_update_f32(float* x, float* r, const float* p, const float* Ap, l
 //                   the last block replaces the recursive residual norm by the
 //                   true one (scaled by sigma^2) and decides convergence.  With
 //                   init = 1 it also starts the solve (sigma = 1/||b||, iter = 0).
+//                   project = 1 removes the mean (singular pressure system).
 //   rel_convert:    r32 = sigma (r64 - mean)
 cudaError_t rel_accumulate(double* x64, float* x32, long long n, const SolverState* st, cudaStream_t s);
 cudaError_t rel_residual(const double* b, const double* Ax, double* r64, long long n, SolverState* st,
-                         double* partials, double rtol, int maxit, double delta, int init, cudaStream_t s);
+                         double* partials, double rtol, int maxit, double delta, int init, int project,
+                         cudaStream_t s);
 cudaError_t rel_convert(const double* r64, float* r32, long long n, const SolverState* st, cudaStream_t s);
+
+// Restore the component of x in the kernel of the periodic pressure operator
+// to that of x0: c = (1/ncell) (P1 (x) ... (x) P1) sum_e (x - x0)[e], then
+// x[e] -= c for every element (P1: 1D kernel projector, kproj).
+cudaError_t kernel_restore(const sdg_handle* h, double* x, const double* x0, cudaStream_t s, int* launches);
 
 // step stages
 cudaError_t k_dual_to_main(const sdg_handle* h, int d, const double* in, double* out, cudaStream_t s);

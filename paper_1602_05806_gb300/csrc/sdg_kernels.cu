@@ -16,6 +16,14 @@ inline unsigned grid_for(long long n) {
   return (unsigned)b;
 }
 
+// grid of the vectorised CG update: enough blocks to fill the machine
+inline unsigned grid_vec(long long n, int w) {
+  long long b = (n / w + kThreads - 1) / kThreads;
+  if (b > kReduceBlocks) b = kReduceBlocks;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
 inline unsigned grid_full(long long n) {
   long long b = (n + kThreads - 1) / kThreads;
   return (unsigned)(b < 1 ? 1 : b);
@@ -60,19 +68,45 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 template <typename T>
+struct V4;
+template <>
+struct V4<float> { using V = float4; static constexpr int W = 4; };
+template <>
+struct V4<double> { using V = double2; static constexpr int W = 2; };
+
+template <typename T>
+__device__ __forceinline__ void upd1(T& x, T& r, T p, T Ap, T alpha, double& rr) {
+  x = fma(alpha, p, x);
+  r = fma(-alpha, Ap, r);
+  rr += (double)r * (double)r;
+}
+
+// x += alpha p ; r -= alpha Ap ; rr = r.r  (vectorised, scalar tail)
+template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_cg_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ Ap,
                 long long n, SolverState* st, double* partials) {
   if (st->done || st->pause) return;
+  using V = typename V4<T>::V;
+  constexpr int W = V4<T>::W;
   const T alpha = (T)st->alpha;
   double rr = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    x[i] = fma(alpha, p[i], x[i]);
-    const T ri = fma(-alpha, Ap[i], r[i]);
-    r[i] = ri;
-    rr += (double)ri * (double)ri;
+  const long long nv = n / W;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  for (long long i = tid; i < nv; i += nth) {
+    V xv = reinterpret_cast<V*>(x)[i], rv = reinterpret_cast<V*>(r)[i];
+    const V pv = reinterpret_cast<const V*>(p)[i], av = reinterpret_cast<const V*>(Ap)[i];
+    T* xs = reinterpret_cast<T*>(&xv);
+    T* rs = reinterpret_cast<T*>(&rv);
+    const T* ps = reinterpret_cast<const T*>(&pv);
+    const T* as = reinterpret_cast<const T*>(&av);
+#pragma unroll
+    for (int k = 0; k < W; ++k) upd1(xs[k], rs[k], ps[k], as[k], alpha, rr);
+    reinterpret_cast<V*>(x)[i] = xv;
+    reinterpret_cast<V*>(r)[i] = rv;
   }
+  for (long long i = nv * W + tid; i < n; i += nth) upd1(x[i], r[i], p[i], Ap[i], alpha, rr);
   double v[1] = {rr}, tot[1];
   if (grid_sum<1>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
     const double rr = tot[0];
@@ -114,7 +148,7 @@ __global__ void __launch_bounds__(kThreads)
 __global__ void __launch_bounds__(kThreads)
     k_rel_residual(const double* __restrict__ b, const double* __restrict__ Ax, double* __restrict__ r,
                    long long n, SolverState* st, double* partials, double rtol, int maxit, double delta,
-                   int init) {
+                   int init, int project) {
   double s = 0.0, ss = 0.0, bb = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
@@ -127,7 +161,8 @@ __global__ void __launch_bounds__(kThreads)
   }
   double v[3] = {s, ss, bb}, tot[3];
   if (grid_sum<3>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
-    const double mean = tot[0] / (double)n;
+    // singular (periodic pressure) system: the constant part of r is round-off
+    const double mean = project ? tot[0] / (double)n : 0.0;
     double rrp = tot[1] - (double)n * mean * mean;
     if (rrp < 0.0) rrp = 0.0;
     if (init) {
@@ -440,7 +475,80 @@ __global__ void __launch_bounds__(kThreads)
   if (grid_sum<1>(v1, partials, &st->counter, tot) && threadIdx.x == 0) st->red[slot] = tot[0];
 }
 
+// ------------------------------------------------------------------ kernel restoration
+// part[b][l] = sum over elements e = b, b + G, ... of (x - x0)[e][l]
+__global__ void __launch_bounds__(kThreads)
+    k_kernel_partial(Geo g, const double* __restrict__ x, const double* __restrict__ x0, double* part) {
+  const int G = gridDim.x;
+  for (int l = threadIdx.x; l < g.npe; l += blockDim.x) {
+    double acc = 0.0;
+    for (long long e = blockIdx.x; e < g.ncell; e += G) {
+      const long long i = e * g.npe + l;
+      acc += x[i] - x0[i];
+    }
+    part[(size_t)blockIdx.x * g.npe + l] = acc;
+  }
+}
+
+// One block: S = sum_b part[b]; corr = (1/ncell) (P1 (x) P1 (x) P1) S
+__global__ void __launch_bounds__(kThreads)
+    k_kernel_finalize(Geo g, const double* part, int G, const double* proj, double* corr) {
+  extern __shared__ double sm[];
+  double* A = sm;            // npe
+  double* B = sm + g.npe;    // npe
+  __shared__ double P1[kMaxN1 * kMaxN1];
+  const int n1 = g.n1;
+  for (int i = threadIdx.x; i < n1 * n1; i += blockDim.x) P1[i] = proj[i];
+  for (int l = threadIdx.x; l < g.npe; l += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < G; ++b) s += part[(size_t)b * g.npe + l];
+    A[l] = s;
+  }
+  __syncthreads();
+  for (int d = 0; d < g.dim; ++d) {
+    const int st = d == 0 ? 1 : (d == 1 ? n1 : n1 * n1);
+    for (int l = threadIdx.x; l < g.npe; l += blockDim.x) {
+      const int m = (l / st) % n1;
+      const int base = l - m * st;
+      double t = 0.0;
+      for (int q = 0; q < n1; ++q) t += P1[m * n1 + q] * A[base + q * st];
+      B[l] = t;
+    }
+    __syncthreads();
+    double* T = A;
+    A = B;
+    B = T;
+  }
+  for (int l = threadIdx.x; l < g.npe; l += blockDim.x) corr[l] = A[l] / (double)g.ncell;
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_kernel_subtract(Geo g, double* __restrict__ x, const double* __restrict__ corr) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.ndof;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] -= corr[i % g.npe];
+}
+
 }  // namespace
+
+cudaError_t kernel_restore(const sdg_handle* h, double* x, const double* x0, cudaStream_t s, int* launches) {
+  const Geo& g = h->g;
+  const int G = (int)(g.ncell < kKernelBlocks ? g.ncell : kKernelBlocks);
+  k_kernel_partial<<<G, kThreads, 0, s>>>(g, x, x0, h->kpart);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smem = 2 * (size_t)g.npe * sizeof(double);
+  if (smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_kernel_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_kernel_finalize<<<1, kThreads, smem, s>>>(g, h->kpart, G, h->kproj, h->kcorr);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_kernel_subtract<<<grid_for(g.ndof), kThreads, 0, s>>>(g, x, h->kcorr);
+  *launches += 3;
+  return cudaGetLastError();
+}
 
 // ------------------------------------------------------------------ launchers
 cudaError_t cg_init_f64(const double* b, const double* Ax, double* r, long long n, SolverState* st,
@@ -455,12 +563,12 @@ cudaError_t cg_init_f32(const float* b, const float* Ax, float* r, long long n, 
 }
 cudaError_t cg_update_f64(double* x, double* r, const double* p, const double* Ap, long long n,
                           SolverState* st, double* partials, cudaStream_t s) {
-  k_cg_update<double><<<grid_for(n), kThreads, 0, s>>>(x, r, p, Ap, n, st, partials);
+  k_cg_update<double><<<grid_vec(n, 2), kThreads, 0, s>>>(x, r, p, Ap, n, st, partials);
   return cudaGetLastError();
 }
 cudaError_t cg_update_f32(float* x, float* r, const float* p, const float* Ap, long long n,
                           SolverState* st, double* partials, cudaStream_t s) {
-  k_cg_update<float><<<grid_for(n), kThreads, 0, s>>>(x, r, p, Ap, n, st, partials);
+  k_cg_update<float><<<grid_vec(n, 4), kThreads, 0, s>>>(x, r, p, Ap, n, st, partials);
   return cudaGetLastError();
 }
 cudaError_t rel_accumulate(double* x64, float* x32, long long n, const SolverState* st, cudaStream_t s) {
@@ -468,8 +576,10 @@ cudaError_t rel_accumulate(double* x64, float* x32, long long n, const SolverSta
   return cudaGetLastError();
 }
 cudaError_t rel_residual(const double* b, const double* Ax, double* r64, long long n, SolverState* st,
-                         double* partials, double rtol, int maxit, double delta, int init, cudaStream_t s) {
-  k_rel_residual<<<grid_for(n), kThreads, 0, s>>>(b, Ax, r64, n, st, partials, rtol, maxit, delta, init);
+                         double* partials, double rtol, int maxit, double delta, int init, int project,
+                         cudaStream_t s) {
+  k_rel_residual<<<grid_for(n), kThreads, 0, s>>>(b, Ax, r64, n, st, partials, rtol, maxit, delta, init,
+                                                  project);
   return cudaGetLastError();
 }
 cudaError_t rel_convert(const double* r64, float* r32, long long n, const SolverState* st, cudaStream_t s) {

@@ -27,7 +27,7 @@ SDG_MIXED = 1
 
 # every symbol include/sdg.h declares
 EXPORTS = (
-    "sdg_nodes", "sdg_matrices", "sdg_create", "sdg_destroy", "sdg_set_options",
+    "sdg_nodes", "sdg_matrices", "sdg_kernel_projector", "sdg_create", "sdg_destroy", "sdg_set_options",
     "sdg_set_mixed_options", "sdg_ndof", "sdg_set_state", "sdg_get_state",
     "sdg_pressure_apply", "sdg_viscous_apply", "sdg_pressure_cg", "sdg_viscous_cg",
     "sdg_dual_to_main", "sdg_main_to_dual", "sdg_convect", "sdg_pressure_rhs",
@@ -74,6 +74,7 @@ def lib():
         vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
         L.sdg_nodes.argtypes = [ip, dp, dp]
         L.sdg_matrices.argtypes = [ip, dp]
+        L.sdg_kernel_projector.argtypes = [ip, dp, ctypes.POINTER(ctypes.c_int)]
         L.sdg_create.argtypes = [ctypes.POINTER(sdg_grid), ip, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_double, ctypes.POINTER(vp)]
         L.sdg_destroy.argtypes = [vp]
@@ -153,6 +154,14 @@ def sdg_matrices(N):
     check(lib().sdg_matrices(N, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     names = ("M", "Rt", "Lt", "Rb", "Lb", "ML", "MR", "HR", "HL", "HC")
     return {k: out[i * m:(i + 1) * m].reshape(N + 1, N + 1).copy() for i, k in enumerate(names)}
+
+
+def sdg_kernel_projector(N):
+    """(projector onto ker(R~ - L~) as an (N+1)x(N+1) array, its dimension)."""
+    P = np.zeros((N + 1) * (N + 1))
+    d = ctypes.c_int()
+    check(lib().sdg_kernel_projector(N, P.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(d)))
+    return P.reshape(N + 1, N + 1), d.value
 
 
 class Handle:

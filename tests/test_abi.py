@@ -57,3 +57,26 @@ def test_host_setup_matches_oracle(libpath):
         for k, v in m.items():
             ref = getattr(B, k)
             assert np.abs(v - ref).max() <= 1e-13 * max(1.0, np.abs(ref).max()), (N, k)
+
+
+def test_kernel_projector_matches_oracle_kernel(libpath):
+    """The library's 1D kernel projector (Jacobi on the host) spans exactly
+    the cell-repeated patterns that the oracle's dense operator annihilates:
+    its dimension is 1 for even N and 2 for odd N, and repeating any
+    projected pattern in every cell gives a kernel vector of the oracle."""
+    import math
+    import numpy as np
+    from oracle import Grid, Oracle
+    from paper_1602_05806_gb300 import sdg
+    for N in range(12):
+        P1, dim = sdg.sdg_kernel_projector(N)
+        assert dim == (1 if N % 2 == 0 else 2)
+        assert np.allclose(P1, P1.T, atol=1e-13) and np.allclose(P1 @ P1, P1, atol=1e-12)
+        assert abs(np.trace(P1) - dim) < 1e-12
+        o = Oracle(Grid(2, (3, 4), (1.0, 1.3)), N, 0.1, 0.6, 0.01)
+        rng = np.random.default_rng(N)
+        c = P1 @ rng.standard_normal((N + 1, N + 1)) @ P1  # local 2D pattern in ker (x) ker
+        x = np.broadcast_to(c, o.shape).copy()
+        Ax = o.pressure_apply(x)
+        scale = np.abs(o.dense(o.pressure_apply)).max() if N <= 4 else 1e3
+        assert np.abs(Ax).max() <= 1e-11 * scale * max(1.0, np.abs(x).max())
