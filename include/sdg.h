@@ -114,14 +114,22 @@ int sdg_destroy(sdg_handle* h);
  *              reduction of every dot product; the correction is folded into
  *              the FP64 solution and the true residual b - A x is recomputed
  *              in FP64 ("reliable update") whenever the FP32 residual has
- *              dropped by the factor delta since the last update; stops when
- *              the true FP64 residual meets the tolerance.
+ *              dropped by the factor delta since the last update (or after
+ *              max(2000, iterations/8) FP32 iterations); stops when the true
+ *              FP64 residual meets the tolerance, or, once it no longer
+ *              improves 2x over two updates (its FP64 round-off floor,
+ *              about eps64 ||A|| ||x||), reports OK if it is within 10 rtol.
+ *              (Plain FP64 CG stops on its recursive residual, whose true
+ *              counterpart can be far larger on ill-conditioned systems.)
  * Defaults: SDG_FP64, 1e-12, 1e-12, 1000000.  Errors: INVALID_ARG. */
 int sdg_set_options(sdg_handle* h, int precision, double rtol_p, double rtol_v,
                     int maxit);
-/* Mixed mode: reliable-update factor delta in (0,1) (default 0.1) and the
- * cap on FP64 residual replacements per solve (default 1000). */
-int sdg_set_mixed_options(sdg_handle* h, double delta, int max_updates);
+/* Mixed mode: reliable-update factor delta in (0,1) (default 0.1), the cap
+ * on FP64 residual replacements per solve (default 1000), and deflate != 0
+ * to remove the kernel of the pressure operator (odd N: constants and
+ * sawtooth patterns) from every FP32 search direction (default 0: the
+ * operator kernel already annihilates those patterns exactly). */
+int sdg_set_mixed_options(sdg_handle* h, double delta, int max_updates, int deflate);
 
 /* Number of DOF of one field (ncell * n1^dim). */
 long long sdg_ndof(const sdg_handle* h);

@@ -38,6 +38,7 @@ Readings of points the paper leaves open (each is exercised by a test):
 from __future__ import annotations
 
 import dataclasses
+import itertools
 import math
 
 import numpy as np
@@ -459,6 +460,123 @@ class Oracle:
         for d in range(self.dim):
             tot += 0.5 * cellvol * float(np.sum(self.mass_all(Us[d] * Us[d])))
         return tot / vol
+
+    # ------------------------------------------------------------- exact periodic solves
+    def kernel_patterns(self):
+        """Orthonormal local patterns (rows) whose repetition in every element
+        spans the kernel of the periodic pressure operator: tensor products of
+        a basis of null(R~ - L~) (Sec. 2.1: weak solutions of grad p = 0)."""
+        G = self.B.Rt - self.B.Lt
+        _, sv, vt = np.linalg.svd(G)
+        tol = 1e-10 * max(1.0, np.abs(self.B.Rt).max())
+        null1 = vt[sv <= tol]  # rows: orthonormal basis of null(G)
+        pats = []
+        for idx in itertools.product(range(null1.shape[0]), repeat=self.dim):
+            p = np.ones(())
+            for d in reversed(range(self.dim)):  # local axes ordered (l_{dim-1}, ..., l_0)
+                p = np.multiply.outer(p, null1[idx[d]])
+            pats.append(p.reshape(-1))
+        return np.array(pats)
+
+    def kernel_part(self, X):
+        """Euclidean projection of X onto the kernel (element-repeated
+        patterns of kernel_patterns)."""
+        K = self.kernel_patterns()
+        npe = self.n1 ** self.dim
+        Xe = X.reshape(-1, npe)
+        coef = K @ Xe.sum(axis=0) / Xe.shape[0]
+        return np.broadcast_to(K.T @ coef, Xe.shape).reshape(X.shape)
+
+    def _symbols(self, d):
+        """W^{-1/2} (H^L e^{-ik} + H^C + H^R e^{ik}) W^{-1/2} eigen-decomposed
+        for every wavenumber k = 2 pi m / n_d (numpy FFT ordering)."""
+        B = self.B
+        n = self.g.n[d]
+        ws = 1.0 / np.sqrt(B.w)
+        lam, vec = [], []
+        for m in range(n):
+            k = 2.0 * math.pi * m / n
+            S = B.HL * np.exp(-1j * k) + B.HC + B.HR * np.exp(1j * k)
+            S = 0.5 * (S + S.conj().T)
+            e, V = np.linalg.eigh(ws[:, None] * S * ws[None, :])
+            lam.append(e)
+            vec.append(V)
+        return np.array(lam), np.array(vec)  # (n, n1), (n, n1, n1)
+
+    def block_circulant_solve(self, b, x0, cmass, scale):
+        """Exact solution of (cmass M^{xyz} + scale * A') x = b on the periodic
+        grid, A' = dt sum_d (1/dx_d^2) M^{perp d} H_d (Eq. pSyst).  The operator
+        is block-circulant: a discrete Fourier transform over the elements of
+        each direction turns it into one n1^dim x n1^dim Hermitian block per
+        wave vector, W^{1/2} [cmass I + sum_d scale dt/dx_d^2 (S_d(k_d) in
+        direction d)] W^{1/2} with S_d = W^{-1/2} (H^L e^{-ik} + H^C +
+        H^R e^{ik}) W^{-1/2}, which the 1D eigenvectors of the S_d
+        diagonalise.  Zero eigenvalues (the kernel, cmass = 0) are dropped and
+        the kernel part of x0 is kept, as CG from x0 does."""
+        dim = self.dim
+        eax = [self._eax(d) for d in range(dim)]
+        lax = [self._lax(d) for d in range(dim)]
+        w = self.B.w
+        sq = np.sqrt(w)
+        # D^{-1} = W^{-1/2} in every direction
+        Bh = np.fft.fftn(b, axes=eax)
+        for d in range(dim):
+            shp = [1] * (2 * dim)
+            shp[lax[d]] = self.n1
+            Bh = Bh / sq.reshape(shp)
+        syms = [self._symbols(d) for d in range(dim)]
+        # transform to the eigenbasis of each direction (per wavenumber)
+        def along_batched(X, V, d, conj):
+            # X[..., e_d, ..., l_d, ...]; V[e_d] is (n1 x n1): X_l <- sum_k M[e][l][k] X_k
+            Xm = np.moveaxis(np.moveaxis(X, eax[d], 0), lax[d] if lax[d] > eax[d] else lax[d] + 1, -1)
+            M = V.conj().transpose(0, 2, 1) if conj else V  # (n, n1, n1)
+            shp = (M.shape[0],) + (1,) * (Xm.ndim - 2) + M.shape[1:]
+            Y = np.einsum('e...k,e...lk->e...l', Xm, M.reshape(shp))
+            Y = np.moveaxis(Y, -1, lax[d] if lax[d] > eax[d] else lax[d] + 1)
+            return np.moveaxis(Y, 0, eax[d])
+        Y = Bh
+        for d in range(dim):
+            Y = along_batched(Y, syms[d][1], d, conj=True)
+        den = np.full(Y.shape, cmass, dtype=np.float64)
+        for d in range(dim):
+            lam = syms[d][0]  # (n_d, n1)
+            shp = [1] * (2 * dim)
+            shp[eax[d]] = lam.shape[0]
+            shp[lax[d]] = self.n1
+            den = den + scale * self.dt / self.g.dx[d] ** 2 * lam.reshape(shp)
+        tol = 1e-11 * np.abs(den).max()
+        Y = np.where(np.abs(den) > tol, Y / np.where(np.abs(den) > tol, den, 1.0), 0.0)
+        for d in range(dim):
+            Y = along_batched(Y, syms[d][1], d, conj=False)
+        for d in range(dim):
+            shp = [1] * (2 * dim)
+            shp[lax[d]] = self.n1
+            Y = Y / sq.reshape(shp)
+        x = np.real(np.fft.ifftn(Y, axes=eax))
+        if cmass == 0.0:
+            x = x - self.kernel_part(x) + self.kernel_part(x0)
+        return x
+
+    def pressure_solve_exact(self, b, x0):
+        """theta A' x = b solved exactly (block_circulant_solve)."""
+        return self.block_circulant_solve(b, x0, 0.0, self.theta)
+
+    def viscous_solve_exact(self, b):
+        """(M + nu A') x = b solved exactly (block_circulant_solve)."""
+        return self.block_circulant_solve(b, b, 1.0, self.nu)
+
+    def step_exact(self, Us, P):
+        """`step` with both linear systems solved exactly instead of by CG."""
+        V = [self.dual_to_main(Us[d], d) for d in range(self.dim)]
+        F = self.rk3(V)
+        Vh = [self.viscous_solve_exact(self.mass_all(F[c])) for c in range(self.dim)]
+        Ustar = [self.main_to_dual(Vh[d], d) for d in range(self.dim)]
+        b = self.pressure_rhs(Ustar, P)
+        b = b - np.mean(b)
+        x = self.pressure_solve_exact(b, P)
+        Pn = x - self.physical_mean(x)
+        q = self.theta * Pn + (1.0 - self.theta) * P
+        return self.velocity_update(Ustar, q), Pn
 
     # ------------------------------------------------------------- dense assembly
     def dense(self, apply):

@@ -2,8 +2,10 @@
 // FP32-inner / FP64-refined) and the fractional time step of Sec. 2.3.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "sdg_internal.h"
 
@@ -78,8 +80,10 @@ extern "C" const char* sdg_strerror(int status);
 namespace {
 
 template <typename T>
-cudaError_t apply_plain(const sdg_handle* h, const Op& op, const T* x, T* y, cudaStream_t s) {
+cudaError_t apply_plain(const sdg_handle* h, const Op& op, const T* x, T* y, cudaStream_t s,
+                        int accurate = 0) {
   ApplyArgs<T> a{};
+  a.accurate = accurate;
   a.x = x;
   a.y = y;
   for (int d = 0; d < 3; ++d) a.s[d] = op.s[d];
@@ -103,7 +107,17 @@ cudaError_t apply_plain(const sdg_handle* h, const Op& op, const T* x, T* y, cud
 // batch of iterations.  Returns with h->st_host[sid] current.
 template <typename T>
 int cg_loop(sdg_handle* h, const Op& op, T* x, T* r, T* const* p, T* Ap, int sid, cudaStream_t s,
-            long long* launched_io) {
+            long long* launched_io, bool deflate = false, long long segment_cap = 0) {
+  const int iter_start = h->st_host[sid].iter;
+  Deflate df{};
+  if (deflate) {
+    df.kpart = h->kdpart;
+    df.kbasis = h->kbasis;
+    df.kc = h->kc;
+    df.npe = h->g.npe;
+    df.kd = h->kd;
+    df.ncell = h->g.ncell;
+  }
   SolverState* st = st_dev(h, sid);
   double* pa = parts(h, sid);
   const long long n = h->g.ndof;
@@ -129,6 +143,7 @@ int cg_loop(sdg_handle* h, const Op& op, T* x, T* r, T* const* p, T* Ap, int sid
       a.fuse = 1;
       a.st = st;
       a.partials = pa;
+      a.kc = deflate ? h->kc : nullptr;
       if (prof) SDG_CK(cudaEventRecord(h->pev[2 * k], s));
       if constexpr (sizeof(T) == 8) {
         SDG_K(launch_apply_f64(h, a, s));
@@ -137,7 +152,7 @@ int cg_loop(sdg_handle* h, const Op& op, T* x, T* r, T* const* p, T* Ap, int sid
       } else {
         SDG_K(launch_apply_f32(h, a, s));
         if (prof) SDG_CK(cudaEventRecord(h->pev[2 * k + 1], s));
-        SDG_K(cg_update_f32(x, r, p[(launched + 1) & 1], Ap, n, st, pa, s));
+        SDG_K(cg_update_f32(x, r, p[(launched + 1) & 1], Ap, n, st, pa, df, s));
       }
       ++launched;
     }
@@ -157,6 +172,7 @@ int cg_loop(sdg_handle* h, const Op& op, T* x, T* r, T* const* p, T* Ap, int sid
     iter_before = hs.iter;
     launched = hs.iter;
     if (hs.done || hs.pause) break;
+    if (segment_cap > 0 && hs.iter - iter_start >= segment_cap) break;  // caller replaces the residual
     if (batch < 32) batch *= 2;
   }
   return SDG_OK;
@@ -204,6 +220,9 @@ int solve_mixed(sdg_handle* h, const Op& op, const double* b, double* x, double 
                 sdg_cg_info* info, cudaStream_t s, bool singular) {
   const long long n = h->g.ndof;
   if (singular) SDG_CK(cudaMemcpyAsync(h->x0buf, x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  // deflate the kernel in the FP32 iterations when it is more than the
+  // constants (the constants are annihilated exactly by the operator kernel)
+  const bool deflate = singular && h->kd > 1 && h->deflate;
   SolverState* st = st_dev(h, sid);
   double* pa = parts(h, sid);
   const double delta = h->delta;
@@ -211,26 +230,48 @@ int solve_mixed(sdg_handle* h, const Op& op, const double* b, double* x, double 
   long long launched = 0;
   // start: r = b - A x0, x32 = 0
   SDG_CK(cudaMemsetAsync(h->x32, 0, n * sizeof(float), s));
-  SDG_K(apply_plain<double>(h, op, x, h->Ap64, s));
+  SDG_K(apply_plain<double>(h, op, x, h->Ap64, s, 1));
   ++a64;
   SDG_K(rel_residual(b, h->Ap64, h->r64, n, st, pa, rtol, h->maxit, delta, 1, singular, s));
   SDG_K(rel_convert(h->r64, h->r32, n, st, s));
   h->st_host[sid].iter = 0;
   int status = SDG_OK;
+  double best = -1.0;   // best true relative residual so far
+  int stagnant = 0;     // consecutive replacements without a 2x improvement
   for (;;) {
     SDG_CK(cudaMemcpyAsync(h->st_host + sid, st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
     SDG_CK(cudaStreamSynchronize(s));
     if (h->st_host[sid].done) break;
-    int rc = cg_loop<float>(h, op, h->x32, h->r32, h->p32, h->Ap32, sid, s, &launched);
+    {
+      // the true residual has an FP64 round-off floor (about eps64 ||A|| ||x||):
+      // once it stops improving, stop at the accuracy reached
+      const double cur = std::sqrt(h->st_host[sid].rr);
+      if (best < 0.0 || cur < 0.5 * best) stagnant = 0; else ++stagnant;
+      if (best < 0.0 || cur < best) best = cur;
+      if (stagnant >= 2 && cur <= 10.0 * rtol) break;  // at the round-off floor
+    }
+    // the FP32 residual comes from the FP64 one: its kernel part is round-off
+    if (deflate) SDG_CK(cudaMemsetAsync(h->kc, 0, h->g.npe * sizeof(float), s));
+    // a segment that runs long without the residual dropping by delta is cut
+    // short so that the FP64 residual is checked
+    const long long it_now = h->st_host[sid].iter;
+    const long long cap = it_now / 8 > 2000 ? it_now / 8 : 2000;
+    int rc = cg_loop<float>(h, op, h->x32, h->r32, h->p32, h->Ap32, sid, s, &launched, deflate, cap);
     if (rc != SDG_OK) return rc;
     const SolverState hs = h->st_host[sid];
     // fold the FP32 correction into x and replace the residual (also after
     // a cap or a breakdown, so that x and the reported residual are current)
     SDG_K(rel_accumulate(x, h->x32, n, st, s));
-    SDG_K(apply_plain<double>(h, op, x, h->Ap64, s));
+    SDG_K(apply_plain<double>(h, op, x, h->Ap64, s, 1));
     ++a64;
     SDG_K(rel_residual(b, h->Ap64, h->r64, n, st, pa, rtol, h->maxit, delta, 0, singular, s));
     ++updates;
+    if (h->verbose) {
+      SDG_CK(cudaMemcpyAsync(h->st_host + sid, st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+      SDG_CK(cudaStreamSynchronize(s));
+      std::fprintf(stderr, "sdg: reliable update %d at FP32 iteration %d: true ||r||/||b|| = %.3e\n", updates,
+                   h->st_host[sid].iter, std::sqrt(h->st_host[sid].rr));
+    }
     if (hs.done || updates >= h->max_updates) {
       // the FP32 iteration hit maxit or broke down, or the update cap is
       // reached: report the true residual of the final x
@@ -253,7 +294,7 @@ int solve_mixed(sdg_handle* h, const Op& op, const double* b, double* x, double 
     h->launches += nl;
   }
   const SolverState& hs = h->st_host[sid];
-  if (status == SDG_OK) status = hs.status;
+  if (status == SDG_OK && hs.done) status = hs.status;
   fill_info(info, hs, updates, a64, hs.iter, status);
   return status;
 }
@@ -372,6 +413,13 @@ int sdg_create(const sdg_grid* grid, int N, double nu, double theta, double dt, 
   h->maxit = 1000000;
   h->max_updates = 1000;
   build_basis(N, &h->basis);
+  build_coefs(h->basis, 0, &h->coef64);
+  build_coefs(h->basis, 1, &h->coef32);
+  h->deflate = 0;
+  {
+    const char* v = std::getenv("SDG_VERBOSE");
+    h->verbose = (v && v[0] == '1') ? 1 : 0;
+  }
 
   const long long n = h->g.ndof;
   // the operator kernel has one CTA per element box; the smallest box is one
@@ -393,6 +441,8 @@ int sdg_create(const sdg_grid* grid, int N, double nu, double theta, double dt, 
   A_(h->kpart, (size_t)kKernelBlocks * h->g.npe);
   A_(h->kcorr, h->g.npe);
   A_(h->kproj, h->g.n1 * h->g.n1);
+  A_(h->kdpart, (size_t)kDeflateBlocks * h->g.npe);
+  A_(h->kc, h->g.npe);
 #undef A_
   if (rc != SDG_OK) { sdg_destroy(h); return rc; }
   if (cudaMallocHost(&h->st_host, kMaxStates * sizeof(SolverState)) != cudaSuccess) {
@@ -416,9 +466,28 @@ int sdg_create(const sdg_grid* grid, int N, double nu, double theta, double dt, 
   for (int k = 0; k < 11; ++k) std::memcpy(table + ids[k] * kMatStride, mats[k], n1 * n1 * sizeof(double));
   cudaError_t e = cudaMemcpy(h->mats, table, sizeof(table), cudaMemcpyHostToDevice);
   {
-    double proj[kMaxN1 * kMaxN1];
+    double proj[kMaxN1 * kMaxN1], b1[kMaxN1 * kMaxN1];
     h->kdim = kernel_projector(h->basis, proj);
     if (e == cudaSuccess) e = cudaMemcpy(h->kproj, proj, n1 * n1 * sizeof(double), cudaMemcpyHostToDevice);
+    // local kernel patterns: tensor products of the 1D basis vectors
+    const int kd1 = kernel_basis(h->basis, b1);
+    const int npe = h->g.npe;
+    h->kd = 1;
+    for (int d = 0; d < h->dim; ++d) h->kd *= kd1;
+    std::vector<double> kb((size_t)h->kd * npe);
+    for (int j = 0; j < h->kd; ++j) {
+      int jj = j, idx[3] = {0, 0, 0};
+      for (int d = 0; d < h->dim; ++d) { idx[d] = jj % kd1; jj /= kd1; }
+      for (int l = 0; l < npe; ++l) {
+        int ll = l;
+        double v = 1.0;
+        for (int d = 0; d < h->dim; ++d) { v *= b1[idx[d] * n1 + ll % n1]; ll /= n1; }
+        kb[(size_t)j * npe + l] = v;
+      }
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&h->kbasis, kb.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(h->kbasis, kb.data(), kb.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(h->kc, 0, npe * sizeof(float));
   }
   if (e == cudaSuccess) e = cudaMemset(h->st, 0, kMaxStates * sizeof(SolverState));
   for (int d = 0; d < h->dim && e == cudaSuccess; ++d) e = cudaMemset(h->U[d], 0, n * sizeof(double));
@@ -451,6 +520,7 @@ int sdg_destroy(sdg_handle* h) {
   cudaFree(h->x32); cudaFree(h->r32); cudaFree(h->p32[0]); cudaFree(h->p32[1]); cudaFree(h->Ap32);
   cudaFree(h->st); cudaFree(h->partials); cudaFree(h->mats);
   cudaFree(h->x0buf); cudaFree(h->kpart); cudaFree(h->kcorr); cudaFree(h->kproj);
+  cudaFree(h->kbasis); cudaFree(h->kdpart); cudaFree(h->kc);
   if (h->st_host) cudaFreeHost(h->st_host);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
@@ -474,12 +544,13 @@ int sdg_set_options(sdg_handle* h, int precision, double rtol_p, double rtol_v, 
   return SDG_OK;
 }
 
-int sdg_set_mixed_options(sdg_handle* h, double delta, int max_updates) {
+int sdg_set_mixed_options(sdg_handle* h, double delta, int max_updates, int deflate) {
   SDG_ARG(h, "NULL handle");
   SDG_ARG(delta > 0.0 && delta < 1.0, "delta must be in (0, 1)");
   SDG_ARG(max_updates >= 1, "max_updates must be >= 1");
   h->delta = delta;
   h->max_updates = max_updates;
+  h->deflate = deflate ? 1 : 0;
   return SDG_OK;
 }
 

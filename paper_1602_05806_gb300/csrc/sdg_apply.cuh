@@ -39,14 +39,14 @@ struct Tile {
   static constexpr int NSLOT = TE + 2 * TY * TZ + 2 * TX * TZ + (DIM == 3 ? 2 * TX * TY : 0);
 };
 
-// Stored 1D blocks in the compute precision: H^C symmetric and H^L equal to
-// (H^R)^T exactly, so the stored operator is exactly symmetric; rho[m] is the
-// row sum of the stored [H^L H^C H^R] (zero in exact arithmetic, a few ulps
-// after rounding).
+// Stored 1D blocks in the compute precision (see CoefSet): H^C symmetric and
+// H^L = (H^R)^T exactly; rho the row sums of [H^L H^C H^R]; for odd N the
+// stored sawtooth pattern z, zn = z / (z.z) and the symmetric correction C.
 template <typename T, int N1>
 struct Coef {
   T HL[N1 * N1], HC[N1 * N1], HR[N1 * N1];
-  T rho[N1];
+  T C[(N1 % 2 == 0) ? N1 * N1 : 1];
+  T rho[N1], z[N1], zn[N1];
 };
 
 template <typename T, int DIM, int N1>
@@ -64,6 +64,7 @@ struct ApplyParams {
   int fuse;
   SolverState* st;
   double* partials;
+  const float* kc;  // FP32 CG: kernel part of r per local node (null = off)
 };
 
 template <typename T>
@@ -136,7 +137,10 @@ __device__ __forceinline__ bool slot_elem(int s, const int o[3], int VX, int VY,
   return true;
 }
 
-template <typename T, int DIM, int N1>
+// ACC: accurate contraction (local kernel removal + symmetric correction),
+// used for every FP32 application and for the FP64 true residuals of the
+// mixed solver; plain FP64 CG uses the direct contraction.
+template <typename T, int DIM, int N1, bool ACC>
 __global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
     k_apply(const __grid_constant__ ApplyParams<T, DIM, N1> a) {
   using TS = Tile<DIM, N1>;
@@ -150,8 +154,10 @@ __global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
   T* s_in = reinterpret_cast<T*>(smem_raw);  // NSLOT * NPE
   T* s_out = s_in + NSLOT * NPE;             // TE * NPE
   __shared__ T s_w[N1];
+  __shared__ T s_kc[sizeof(T) == 4 ? NPE : 1];
 
   const bool fuse = a.fuse != 0;
+  const bool defl = sizeof(T) == 4 && fuse && a.kc != nullptr;
   bool first = false;
   T beta = T(0);
   if (fuse) {
@@ -160,6 +166,9 @@ __global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
     beta = first ? T(0) : T(a.st->rr / a.st->rr_old);
   }
   if (threadIdx.x < N1) s_w[threadIdx.x] = a.w[threadIdx.x];
+  if (defl)
+    for (int l = threadIdx.x; l < NPE; l += blockDim.x) s_kc[l] = (T)a.kc[l];
+  __syncthreads();
 
   // tile origin and valid extents
   const int bx = blockIdx.x % a.ntile[0];
@@ -182,6 +191,11 @@ __global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
       val = reinterpret_cast<const V*>(a.x)[gi];
     } else {
       V r = reinterpret_cast<const V*>(a.x)[gi];
+      if (defl) {  // the direction is built from the residual's range part
+        T* rp = reinterpret_cast<T*>(&r);
+#pragma unroll
+        for (int k = 0; k < VW; ++k) rp[k] -= s_kc[off * VW + k];
+      }
       if (first) {
         val = r;
       } else {
@@ -232,21 +246,38 @@ __global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
         xc[k] = s_in[sc * NPE + base + k * stride];
         xr[k] = s_in[sr * NPE + base + k * stride];
       }
-      // Every row of [H^L H^C H^R] sums to zero (the operator annihilates
-      // constants), so a line-wide constant c may be removed before the
-      // contractions.  Subtracting the centre node value shrinks the
-      // operands of smooth fields to their local variation and cuts the
-      // rounding error of the product on smooth modes by orders of magnitude
-      // (it matters in FP32).  The stored blocks' row sums rho are not exactly
-      // zero, so the term rho_m (c - x_m) is added back: the result is
-      // (A - diag(rho)) x, an exactly symmetric operator that annihilates
-      // the constants, whatever c is.
-      const T cref = xc[N1 / 2];
+      // Accuracy of the contraction (it matters in FP32).  The operator
+      // annihilates every line-repeated pattern q in its local kernel: the
+      // constants, and for odd N also the sawtooth z.  So q may be removed
+      // from the three line segments before the contractions: with q fitted
+      // to the centre element (c = centre node value, amplitude dz of z from
+      // the centre segment) the operands shrink to the local variation of
+      // smooth fields, and the rounding of the products drops by orders of
+      // magnitude on the smooth and sawtooth-modulated modes whose
+      // eigenvalues are tiny.  The stored blocks do not annihilate q exactly,
+      // so a symmetric correction is applied to the centre operand: -rho_m
+      // (even N) or C (odd N).  The applied operator is then exactly
+      // symmetric and annihilates q, whatever q is.
+      constexpr bool KZ = ACC && (N1 % 2 == 0);  // odd N: two-dimensional local kernel
+      if constexpr (ACC) {
+        const T cref = xc[N1 / 2];
 #pragma unroll
-      for (int k = 0; k < N1; ++k) {
-        xl[k] -= cref;
-        xc[k] -= cref;
-        xr[k] -= cref;
+        for (int k = 0; k < N1; ++k) {
+          xl[k] -= cref;
+          xc[k] -= cref;
+          xr[k] -= cref;
+        }
+      }
+      if constexpr (KZ) {
+        T dz = T(0);
+#pragma unroll
+        for (int k = 0; k < N1; ++k) dz = fma(a.c.zn[k], xc[k], dz);
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+          xl[k] = fma(-dz, a.c.z[k], xl[k]);
+          xc[k] = fma(-dz, a.c.z[k], xc[k]);
+          xr[k] = fma(-dz, a.c.z[k], xr[k]);
+        }
       }
       const T f = a.s[d] * wp;
       T* out = s_out + te * NPE + base;
@@ -259,10 +290,15 @@ __global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
           acc = fma(a.c.HC[m * N1 + k], xc[k], acc);
           acc = fma(a.c.HR[m * N1 + k], xr[k], acc);
         }
-        acc = fma(-a.c.rho[m], xc[m], acc);
+        if constexpr (KZ) {
+#pragma unroll
+          for (int k = 0; k < N1; ++k) acc = fma(a.c.C[m * N1 + k], xc[k], acc);
+        } else if constexpr (ACC) {
+          acc = fma(-a.c.rho[m], xc[m], acc);
+        }
         T val = f * acc;
         if (d == 0) {
-          val = fma(a.cmass * wp * s_w[m], xc[m] + cref, val);
+          if (a.cmass != T(0)) val = fma(a.cmass * wp * s_w[m], s_in[sc * NPE + base + m * stride], val);
           out[m * stride] = val;
         } else {
           out[m * stride] += val;
@@ -273,7 +309,7 @@ __global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
   }
 
   // ---- store the box (vectorised) and reduce p^T A p ----
-  double dot = 0.0;
+  T dsum = T(0), dcomp = T(0);  // compensated per-thread sum in T
   for (int v = threadIdx.x; v < TE * NV; v += blockDim.x) {
     const int e = v / NV, off = v - e * NV;
     const int ex = e % TX, ey = (e / TX) % TY, ez = e / (TX * TY);
@@ -286,11 +322,16 @@ __global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
       const T* yp = reinterpret_cast<const T*>(&yv);
       const T* pp = reinterpret_cast<const T*>(&pv);
 #pragma unroll
-      for (int k = 0; k < VW; ++k) dot += (double)pp[k] * (double)yp[k];
+      for (int k = 0; k < VW; ++k) {
+        const T yk = fma(pp[k], yp[k], -dcomp);
+        const T t = dsum + yk;
+        dcomp = (t - dsum) - yk;
+        dsum = t;
+      }
     }
   }
   if (fuse) {
-    double v1[1] = {dot}, tot[1];
+    double v1[1] = {(double)dsum - (double)dcomp}, tot[1];
     if (grid_sum<1>(v1, a.partials, &a.st->counter, tot)) {
       if (threadIdx.x == 0) {
         SolverState* st = a.st;
@@ -308,22 +349,23 @@ __global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
   }
 }
 
-template <typename T, int DIM, int N1>
-cudaError_t launch_apply_t(const sdg_handle* h, const ApplyArgs<T>& in, cudaStream_t stream) {
+template <typename T, int DIM, int N1, bool ACC>
+cudaError_t launch_apply_acc(const sdg_handle* h, const ApplyArgs<T>& in, cudaStream_t stream) {
   using TS = Tile<DIM, N1>;
   ApplyParams<T, DIM, N1> p;
   const Basis1D& b = h->basis;
-  for (int m = 0; m < N1; ++m)
-    for (int k = 0; k < N1; ++k) {
-      p.c.HR[m * N1 + k] = (T)b.HR[m * N1 + k];
-      p.c.HL[m * N1 + k] = (T)b.HR[k * N1 + m];  // H^L = (H^R)^T
-      p.c.HC[m * N1 + k] = (T)(0.5 * (b.HC[m * N1 + k] + b.HC[k * N1 + m]));
-    }
+  const CoefSet& cs = sizeof(T) == 4 ? h->coef32 : h->coef64;  // values exact in T
+  for (int i = 0; i < N1 * N1; ++i) {
+    p.c.HL[i] = (T)cs.HL[i];
+    p.c.HC[i] = (T)cs.HC[i];
+    p.c.HR[i] = (T)cs.HR[i];
+  }
+  if constexpr (N1 % 2 == 0)
+    for (int i = 0; i < N1 * N1; ++i) p.c.C[i] = (T)cs.C[i];
   for (int m = 0; m < N1; ++m) {
-    long double rs = 0.0L;
-    for (int k = 0; k < N1; ++k)
-      rs += (long double)p.c.HL[m * N1 + k] + (long double)p.c.HC[m * N1 + k] + (long double)p.c.HR[m * N1 + k];
-    p.c.rho[m] = (T)rs;
+    p.c.rho[m] = (T)cs.rho[m];
+    p.c.z[m] = (T)cs.z[m];
+    p.c.zn[m] = (T)cs.zn[m];
   }
   for (int i = 0; i < N1; ++i) p.w[i] = (T)b.w[i];
   p.x = in.x;
@@ -341,18 +383,29 @@ cudaError_t launch_apply_t(const sdg_handle* h, const ApplyArgs<T>& in, cudaStre
   p.fuse = in.fuse;
   p.st = in.st;
   p.partials = in.partials;
+  p.kc = in.kc;
   const long long nblk = (long long)p.ntile[0] * p.ntile[1] * p.ntile[2];
   if (nblk > h->max_blocks) return cudaErrorInvalidConfiguration;
   const size_t smem = (size_t)(TS::NSLOT + TS::TE) * TS::NPE * sizeof(T);
   static bool attr_set = false;  // per instantiation; smem need is fixed
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_apply<T, DIM, N1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_apply<T, DIM, N1, ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k_apply<T, DIM, N1><<<(unsigned)nblk, TS::THREADS, smem, stream>>>(p);
+  k_apply<T, DIM, N1, ACC><<<(unsigned)nblk, TS::THREADS, smem, stream>>>(p);
   return cudaGetLastError();
+}
+
+template <typename T, int DIM, int N1>
+cudaError_t launch_apply_t(const sdg_handle* h, const ApplyArgs<T>& in, cudaStream_t stream) {
+  if constexpr (sizeof(T) == 4) {
+    return launch_apply_acc<T, DIM, N1, true>(h, in, stream);
+  } else {
+    if (in.accurate) return launch_apply_acc<T, DIM, N1, true>(h, in, stream);
+    return launch_apply_acc<T, DIM, N1, false>(h, in, stream);
+  }
 }
 
 }  // namespace sdg

@@ -229,9 +229,13 @@ void jacobi_eig(int n, double* A, double* lam, double* V) {
 
 }  // namespace
 
-int kernel_projector(const Basis1D& b, double* proj) {
+namespace {
+
+int kernel_eig(const Basis1D& b, std::vector<double>& V, std::vector<double>& lam, double* tol_out) {
   const int n = b.n1;
-  std::vector<double> G(n * n), A(n * n), V(n * n), lam(n);
+  std::vector<double> G(n * n), A(n * n);
+  V.assign(n * n, 0.0);
+  lam.assign(n, 0.0);
   double scale = 0.0;  // size of R~ and L~ (R~ - L~ itself vanishes for N = 1)
   for (int i = 0; i < n * n; ++i) {
     G[i] = b.Rt[i] - b.Lt[i];
@@ -245,16 +249,118 @@ int kernel_projector(const Basis1D& b, double* proj) {
       A[p * n + q] = s;
     }
   jacobi_eig(n, A.data(), lam.data(), V.data());
-  for (int i = 0; i < n * n; ++i) proj[i] = 0.0;
+  *tol_out = 1e-12 * (scale > 0 ? scale : 1.0);
+  return n;
+}
+
+}  // namespace
+
+int kernel_basis(const Basis1D& b, double* basis) {
+  const int n = b.n1;
+  std::vector<double> V, lam;
+  double tol;
+  kernel_eig(b, V, lam, &tol);
   int dim = 0;
-  const double tol = 1e-12 * (scale > 0 ? scale : 1.0);
   for (int j = 0; j < n; ++j) {
     if (std::fabs(lam[j]) > tol) continue;
+    for (int l = 0; l < n; ++l) basis[dim * n + l] = V[l * n + j];
     ++dim;
-    for (int p = 0; p < n; ++p)
-      for (int q = 0; q < n; ++q) proj[p * n + q] += V[p * n + j] * V[q * n + j];
   }
   return dim;
+}
+
+int kernel_projector(const Basis1D& b, double* proj) {
+  const int n = b.n1;
+  double basis[kMaxN1 * kMaxN1];
+  const int dim = kernel_basis(b, basis);
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < n; ++q) {
+      double s = 0.0;
+      for (int j = 0; j < dim; ++j) s += basis[j * n + p] * basis[j * n + q];
+      proj[p * n + q] = s;
+    }
+  return dim;
+}
+
+void build_coefs(const Basis1D& b, int fp32, CoefSet* c) {
+  const int n = b.n1;
+  auto rnd = [fp32](double v) { return fp32 ? (double)(float)v : v; };
+  for (int i = 0; i < kMaxN1 * kMaxN1; ++i) c->HL[i] = c->HC[i] = c->HR[i] = c->C[i] = 0.0;
+  for (int i = 0; i < kMaxN1; ++i) c->rho[i] = c->z[i] = c->zn[i] = 0.0;
+  for (int m = 0; m < n; ++m)
+    for (int k = 0; k < n; ++k) {
+      c->HR[m * n + k] = rnd(b.HR[m * n + k]);
+      c->HL[m * n + k] = rnd(b.HR[k * n + m]);
+      c->HC[m * n + k] = rnd(0.5 * (b.HC[m * n + k] + b.HC[k * n + m]));
+    }
+  std::vector<double> G(n * n);
+  for (int i = 0; i < n * n; ++i) G[i] = c->HL[i] + c->HC[i] + c->HR[i];
+  for (int m = 0; m < n; ++m) {
+    long double rs = 0.0L;
+    for (int k = 0; k < n; ++k) rs += (long double)c->HL[m * n + k] + (long double)c->HC[m * n + k] +
+                                      (long double)c->HR[m * n + k];
+    c->rho[m] = rnd((double)rs);
+  }
+  double kb[kMaxN1 * kMaxN1];
+  const int kd = kernel_basis(b, kb);
+  c->kz = kd >= 2 ? 1 : 0;
+  if (!c->kz) return;
+  // z: the kernel direction orthogonal to the constants, scaled to max 1
+  double best = -1.0;
+  std::vector<double> z(n);
+  for (int j = 0; j < kd; ++j) {
+    double mean = 0.0;
+    for (int l = 0; l < n; ++l) mean += kb[j * n + l];
+    mean /= n;
+    double nrm = 0.0;
+    for (int l = 0; l < n; ++l) nrm += (kb[j * n + l] - mean) * (kb[j * n + l] - mean);
+    if (nrm > best) {
+      best = nrm;
+      for (int l = 0; l < n; ++l) z[l] = kb[j * n + l] - mean;
+    }
+  }
+  double zmax = 0.0;
+  for (int l = 0; l < n; ++l) zmax = std::fmax(zmax, std::fabs(z[l]));
+  double zz = 0.0;
+  for (int l = 0; l < n; ++l) {
+    c->z[l] = rnd(z[l] / zmax);
+    zz += c->z[l] * c->z[l];
+  }
+  for (int l = 0; l < n; ++l) c->zn[l] = rnd(c->z[l] / zz);
+  // orthonormal K = [k0, k1] spanning {1, z_stored} (Gram-Schmidt in FP64)
+  std::vector<double> k0(n, 1.0 / std::sqrt((double)n)), k1(n);
+  double d = 0.0;
+  for (int l = 0; l < n; ++l) d += k0[l] * c->z[l];
+  double nn = 0.0;
+  for (int l = 0; l < n; ++l) { k1[l] = c->z[l] - d * k0[l]; nn += k1[l] * k1[l]; }
+  nn = std::sqrt(nn);
+  for (int l = 0; l < n; ++l) k1[l] /= nn;
+  // S = G K; C = -(S K^T + K S^T - K (K^T S) K^T)
+  std::vector<double> S0(n), S1(n);
+  for (int m = 0; m < n; ++m) {
+    double a = 0.0, bb = 0.0;
+    for (int k = 0; k < n; ++k) { a += G[m * n + k] * k0[k]; bb += G[m * n + k] * k1[k]; }
+    S0[m] = a;
+    S1[m] = bb;
+  }
+  double KS[2][2] = {{0, 0}, {0, 0}};
+  for (int l = 0; l < n; ++l) {
+    KS[0][0] += k0[l] * S0[l]; KS[0][1] += k0[l] * S1[l];
+    KS[1][0] += k1[l] * S0[l]; KS[1][1] += k1[l] * S1[l];
+  }
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < n; ++q) {
+      const double skt = S0[p] * k0[q] + S1[p] * k1[q];
+      const double kst = k0[p] * S0[q] + k1[p] * S1[q];
+      const double kk = k0[p] * (KS[0][0] * k0[q] + KS[0][1] * k1[q]) + k1[p] * (KS[1][0] * k0[q] + KS[1][1] * k1[q]);
+      c->C[p * n + q] = -(skt + kst - kk);
+    }
+  for (int p = 0; p < n; ++p)
+    for (int q = p + 1; q < n; ++q) {
+      const double v = rnd(0.5 * (c->C[p * n + q] + c->C[q * n + p]));
+      c->C[p * n + q] = c->C[q * n + p] = v;
+    }
+  for (int p = 0; p < n; ++p) c->C[p * n + p] = rnd(c->C[p * n + p]);
 }
 
 }  // namespace sdg

@@ -33,4 +33,23 @@ int build_basis(int N, Basis1D* b);
 // dimension (1 for even N: the constants; 2 for odd N).
 int kernel_projector(const Basis1D& b, double* proj);
 
+// Orthonormal basis of the same space: basis[j*n1 + l], j < returned dim.
+int kernel_basis(const Basis1D& b, double* basis);
+
+// 1D blocks of the operator kernel as stored in one compute precision (all
+// values exactly representable in it, kept here as doubles):
+//   HR; HL = HR^T; HC symmetrised                      (exactly symmetric)
+//   rho[m] = row sum of [HL HC HR]                     (zero up to rounding)
+//   kz = 1 for odd N: z = stored local sawtooth pattern (orthogonal to the
+//        constants, max |z| = 1), zn = z / (z.z), and C the symmetric matrix
+//        with (HL + HC + HR + C) q = 0 for q in span{1, z} (exact arithmetic).
+struct CoefSet {
+  double HL[kMaxN1 * kMaxN1], HC[kMaxN1 * kMaxN1], HR[kMaxN1 * kMaxN1], C[kMaxN1 * kMaxN1];
+  double rho[kMaxN1], z[kMaxN1], zn[kMaxN1];
+  int kz;
+};
+
+// fp32 != 0: round every stored value to float first.
+void build_coefs(const Basis1D& b, int fp32, CoefSet* out);
+
 }  // namespace sdg

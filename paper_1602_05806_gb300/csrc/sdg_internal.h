@@ -51,6 +51,7 @@ constexpr int kMatTable = kNumMats * kMatStride;
 
 constexpr int kMaxStates = 8;
 constexpr int kKernelBlocks = 512;     // grid of the per-local-node element sum
+constexpr int kDeflateBlocks = 304;    // grid of the deflated FP32 CG update
 constexpr int kPartialSlots = 4;       // doubles per block in a partials array
 constexpr int kReduceBlocks = 152 * 8; // grid of the vector / reduction kernels
 
@@ -71,6 +72,9 @@ struct sdg_handle {
   double delta;     // mixed: reliable-update factor
   int maxit, max_updates;
   sdg::Basis1D basis;
+  sdg::CoefSet coef64, coef32;   // stored operator blocks per precision
+  int deflate;                   // mixed: deflate the kernel in FP32 iterations
+  int verbose;                   // SDG_VERBOSE=1: log every reliable update to stderr
 
   // state
   double* U[3];
@@ -101,6 +105,10 @@ struct sdg_handle {
   double* kcorr;          // correction pattern (npe)
   double* kproj;          // 1D kernel projector (n1 * n1)
   int kdim;               // dimension of the 1D kernel
+  double* kbasis;         // local kernel patterns (kdim^dim x npe), orthonormal
+  int kd;                 // kdim^dim
+  float* kdpart;          // deflation partial sums (kDeflateBlocks * npe)
+  float* kc;              // deflation correction pattern (npe)
   cudaEvent_t ev0, ev1, ev2, ev3;
   // instrumentation
   long long launches;     // kernels launched by this handle
@@ -118,6 +126,21 @@ namespace sdg {
 // first iteration), p is written to p_out, and p^T y is reduced into
 // st->pAp / st->alpha (the CG step-length); the kernel exits at once when
 // st->done is set.
+// Deflation of the kernel of the periodic pressure operator in the FP32
+// iterations (odd N: the per-cell sawtooth patterns, which FP32 rounding of
+// the stored blocks turns into spurious small eigenvalues).  The update kernel
+// reduces per-local-node sums of the new residual, projects them on the
+// orthonormal local kernel patterns and leaves in kc the kernel part of r
+// (one value per local node, the same in every element); the next fused
+// operator forms p from r - kc.
+struct Deflate {
+  float* kpart;          // per-block, per-local-node partial sums (grid * npe); null = off
+  const double* kbasis;  // kd x npe orthonormal local kernel patterns
+  float* kc;             // npe: kernel part of r per local node
+  int npe, kd;
+  long long ncell;
+};
+
 template <typename T>
 struct ApplyArgs {
   const T* x;      // input (fuse = 0) or r (fuse = 1)
@@ -129,6 +152,8 @@ struct ApplyArgs {
   int fuse;
   SolverState* st;
   double* partials;
+  const float* kc;  // fuse = 1, FP32: subtract kc (per local node) from r; null = off
+  int accurate;     // FP64: use the accurate contraction (FP32 always does)
 };
 
 cudaError_t launch_apply_f64(const sdg_handle* h, const ApplyArgs<double>& a, cudaStream_t s);
@@ -148,7 +173,7 @@ cudaError_t cg_init_f32(const float* b, const float* Ax, float* r, long long n, 
 cudaError_t cg_update_f64(double* x, double* r, const double* p, const double* Ap, long long n,
                           SolverState* st, double* partials, cudaStream_t s);
 cudaError_t cg_update_f32(float* x, float* r, const float* p, const float* Ap, long long n,
-                          SolverState* st, double* partials, cudaStream_t s);
+                          SolverState* st, double* partials, const Deflate& df, cudaStream_t s);
 // FP32 CG with FP64 reliable updates:
 //   rel_accumulate: x64 += x32 / sigma, x32 = 0
 //   rel_residual:   r64 = b - Ax (FP64), mean and ||r - mean|| reduced in FP64;

@@ -74,23 +74,53 @@ struct V4<float> { using V = float4; static constexpr int W = 4; };
 template <>
 struct V4<double> { using V = double2; static constexpr int W = 2; };
 
+// Per-thread accumulator of a dot product: FP64 for FP64 data; for FP32 data
+// a compensated (Kahan) FP32 sum, so that no FP64 arithmetic runs per element
+// (GB300 issues FP64 at 1/64 of the FP32 rate).  Blocks reduce in FP64.
 template <typename T>
-__device__ __forceinline__ void upd1(T& x, T& r, T p, T Ap, T alpha, double& rr) {
+struct DotAcc {
+  double s = 0.0;
+  __device__ __forceinline__ void add(T v) { s = fma((double)v, 1.0, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct DotAcc<float> {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+template <typename T>
+__device__ __forceinline__ void upd1(T& x, T& r, T p, T Ap, T alpha, DotAcc<T>& rr) {
   x = fma(alpha, p, x);
   r = fma(-alpha, Ap, r);
-  rr += (double)r * (double)r;
+  rr.add(r * r);
 }
 
-// x += alpha p ; r -= alpha Ap ; rr = r.r  (vectorised, scalar tail)
+// x += alpha p ; r -= alpha Ap ; rr = r.r  (vectorised, scalar tail).
+// With deflation (FP32, df.kpart != null) the kernel part of the new r is
+// reduced too, removed from rr, and left in df.kc for the next direction.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_cg_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ Ap,
-                long long n, SolverState* st, double* partials) {
+                long long n, SolverState* st, double* partials, Deflate df) {
   if (st->done || st->pause) return;
+  extern __shared__ double s_dyn[];
+  float* s_k = reinterpret_cast<float*>(s_dyn);  // npe floats (deflation)
+  const bool defl = df.kpart != nullptr;
+  if (defl) {
+    for (int l = threadIdx.x; l < df.npe; l += blockDim.x) s_k[l] = 0.0f;
+    __syncthreads();
+  }
   using V = typename V4<T>::V;
   constexpr int W = V4<T>::W;
   const T alpha = (T)st->alpha;
-  double rr = 0.0;
+  DotAcc<T> rr;
   const long long nv = n / W;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
@@ -105,27 +135,92 @@ __global__ void __launch_bounds__(kThreads)
     for (int k = 0; k < W; ++k) upd1(xs[k], rs[k], ps[k], as[k], alpha, rr);
     reinterpret_cast<V*>(x)[i] = xv;
     reinterpret_cast<V*>(r)[i] = rv;
+    if (defl) {
+      const unsigned l0 = (unsigned)((unsigned long long)(i * W) % (unsigned)df.npe);
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        unsigned l = l0 + k;
+        if (l >= (unsigned)df.npe) l -= df.npe;
+        atomicAdd(&s_k[l], (float)rs[k]);
+      }
+    }
   }
-  for (long long i = nv * W + tid; i < n; i += nth) upd1(x[i], r[i], p[i], Ap[i], alpha, rr);
-  double v[1] = {rr}, tot[1];
-  if (grid_sum<1>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
-    const double rr = tot[0];
-    st->rr_old = st->rr;
-    st->rr = rr;
-    st->iter += 1;
-    if (rr > st->maxrr) st->maxrr = rr;
-    if (!isfinite(rr)) {
-      st->done = 1;
-      st->status = SDG_ERR_BREAKDOWN;
-    } else if (rr <= st->tol2) {
-      // plain CG stops here; reliable mode confirms with the FP64 residual
-      if (st->reliable) st->pause = 1;
-      else { st->done = 1; st->status = SDG_OK; }
-    } else if (st->reliable && rr < st->delta2 * st->maxrr) {
-      st->pause = 1;
-    } else if (st->iter >= st->maxit) {
-      st->done = 1;
-      st->status = SDG_ERR_NOT_CONVERGED;
+  for (long long i = nv * W + tid; i < n; i += nth) {
+    upd1(x[i], r[i], p[i], Ap[i], alpha, rr);
+    if (defl) atomicAdd(&s_k[(unsigned)((unsigned long long)i % (unsigned)df.npe)], (float)r[i]);
+  }
+  if (defl) {
+    __syncthreads();
+    for (int l = threadIdx.x; l < df.npe; l += blockDim.x)
+      df.kpart[(size_t)blockIdx.x * df.npe + l] = s_k[l];
+    __threadfence();
+  }
+  double v[1] = {rr.value()}, tot[1];
+  if (grid_sum<1>(v, partials, &st->counter, tot)) {
+    double rK2 = 0.0;
+    if (defl) {
+      // S[l] = sum over blocks of the partial sums, in FP64, by G thread groups
+      const int npe = df.npe;
+      const int G = blockDim.x >= 2 * npe ? blockDim.x / npe : 1;
+      double* S = s_dyn;               // npe
+      double* Gp = s_dyn + npe;        // G * npe
+      __shared__ double s_a[8];
+      __syncthreads();
+      if (G > 1) {
+        const int l = threadIdx.x % npe, g = threadIdx.x / npe;
+        if (g < G) {
+          double acc = 0.0;
+          for (unsigned b = g; b < gridDim.x; b += G) acc += (double)__ldcg(&df.kpart[(size_t)b * npe + l]);
+          Gp[g * npe + l] = acc;
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < npe; q += blockDim.x) {
+          double acc = 0.0;
+          for (int g2 = 0; g2 < G; ++g2) acc += Gp[g2 * npe + q];
+          S[q] = acc;
+        }
+      } else {
+        for (int q = threadIdx.x; q < npe; q += blockDim.x) {
+          double acc = 0.0;
+          for (unsigned b = 0; b < gridDim.x; ++b) acc += (double)__ldcg(&df.kpart[(size_t)b * npe + q]);
+          S[q] = acc;
+        }
+      }
+      __syncthreads();
+      if ((int)threadIdx.x < df.kd) {
+        double a = 0.0;
+        for (int q = 0; q < npe; ++q) a += df.kbasis[threadIdx.x * npe + q] * S[q];
+        s_a[threadIdx.x] = a;
+      }
+      __syncthreads();
+      const double inv = 1.0 / (double)df.ncell;
+      for (int q = threadIdx.x; q < npe; q += blockDim.x) {
+        double c = 0.0;
+        for (int j = 0; j < df.kd; ++j) c += s_a[j] * df.kbasis[j * npe + q];
+        df.kc[q] = (float)(c * inv);
+      }
+      for (int j = 0; j < df.kd; ++j) rK2 += s_a[j] * s_a[j] * inv;
+    }
+    if (threadIdx.x == 0) {
+      double rr = tot[0] - rK2;  // residual norm in the range of the operator
+      if (rr < 0.0) rr = 0.0;
+      st->rr_old = st->rr;
+      st->rr = rr;
+      st->iter += 1;
+      if (rr > st->maxrr) st->maxrr = rr;
+      if (!isfinite(rr)) {
+        st->done = 1;
+        st->status = SDG_ERR_BREAKDOWN;
+      } else if (rr <= st->tol2) {
+        // plain CG stops here; reliable mode confirms with the FP64 residual
+        if (st->reliable) st->pause = 1;
+        else { st->done = 1; st->status = SDG_OK; }
+      } else if (st->reliable && rr < st->delta2 * st->maxrr) {
+        st->pause = 1;
+      } else if (st->iter >= st->maxit) {
+        st->done = 1;
+        st->status = SDG_ERR_NOT_CONVERGED;
+      }
     }
   }
 }
@@ -563,12 +658,28 @@ cudaError_t cg_init_f32(const float* b, const float* Ax, float* r, long long n, 
 }
 cudaError_t cg_update_f64(double* x, double* r, const double* p, const double* Ap, long long n,
                           SolverState* st, double* partials, cudaStream_t s) {
-  k_cg_update<double><<<grid_vec(n, 2), kThreads, 0, s>>>(x, r, p, Ap, n, st, partials);
+  k_cg_update<double><<<grid_vec(n, 2), kThreads, 0, s>>>(x, r, p, Ap, n, st, partials, Deflate{});
   return cudaGetLastError();
 }
 cudaError_t cg_update_f32(float* x, float* r, const float* p, const float* Ap, long long n,
-                          SolverState* st, double* partials, cudaStream_t s) {
-  k_cg_update<float><<<grid_vec(n, 4), kThreads, 0, s>>>(x, r, p, Ap, n, st, partials);
+                          SolverState* st, double* partials, const Deflate& df, cudaStream_t s) {
+  if (df.kpart == nullptr) {
+    k_cg_update<float><<<grid_vec(n, 4), kThreads, 0, s>>>(x, r, p, Ap, n, st, partials, df);
+    return cudaGetLastError();
+  }
+  const int npe = df.npe;
+  const int G = kThreads >= 2 * npe ? kThreads / npe : 1;
+  size_t smem = (size_t)(G + 1) * npe * sizeof(double);
+  if (smem < npe * sizeof(float)) smem = npe * sizeof(float);
+  static size_t attr = 0;
+  if (smem > 48 * 1024 && smem > attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_cg_update<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = smem;
+  }
+  unsigned g = grid_vec(n, 4);
+  if (g > (unsigned)kDeflateBlocks) g = kDeflateBlocks;
+  k_cg_update<float><<<g, kThreads, smem, s>>>(x, r, p, Ap, n, st, partials, df);
   return cudaGetLastError();
 }
 cudaError_t rel_accumulate(double* x64, float* x32, long long n, const SolverState* st, cudaStream_t s) {

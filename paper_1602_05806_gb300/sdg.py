@@ -79,7 +79,7 @@ def lib():
                                  ctypes.c_double, ctypes.POINTER(vp)]
         L.sdg_destroy.argtypes = [vp]
         L.sdg_set_options.argtypes = [vp, ip, ctypes.c_double, ctypes.c_double, ip]
-        L.sdg_set_mixed_options.argtypes = [vp, ctypes.c_double, ip]
+        L.sdg_set_mixed_options.argtypes = [vp, ctypes.c_double, ip, ip]
         L.sdg_ndof.argtypes = [vp]
         L.sdg_ndof.restype = ctypes.c_longlong
         L.sdg_set_state.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -198,8 +198,8 @@ class Handle:
     def set_options(self, precision=SDG_FP64, rtol_p=1e-12, rtol_v=1e-12, maxit=1000000):
         check(lib().sdg_set_options(self.h, precision, rtol_p, rtol_v, maxit))
 
-    def set_mixed_options(self, delta=0.1, max_updates=1000):
-        check(lib().sdg_set_mixed_options(self.h, delta, max_updates))
+    def set_mixed_options(self, delta=0.1, max_updates=1000, deflate=False):
+        check(lib().sdg_set_mixed_options(self.h, delta, max_updates, 1 if deflate else 0))
 
     def set_profiling(self, enable=True):
         check(lib().sdg_set_profiling(self.h, 1 if enable else 0))

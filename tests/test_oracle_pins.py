@@ -494,3 +494,43 @@ def test_step_spatial_order(N):
         errs.append(max(np.abs(Us[c] - U0[c]).max() for c in range(2)))
     orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert min(orders) >= N - 0.25, orders
+
+
+# ------------------------------------------------------------------ exact periodic solves
+@pytest.mark.parametrize("dim,n,N", [(2, (5, 4), 3), (2, (4, 6), 2), (3, (3, 4, 2), 1), (3, (2, 3, 4), 2)])
+def test_block_circulant_solve_matches_dense(dim, n, N):
+    """The exact Fourier solve of the periodic system equals the dense
+    pseudo-inverse solution plus the kernel part of x0 (pressure, Eq. pSyst)
+    and the dense solve of the SPD viscous system (Eq. implicitviscosity)."""
+    o = _oracle(dim, n, N, L=(1.0, 1.4, 0.8)[:dim])
+    A = o.dense(o.pressure_apply)
+    ev, V = np.linalg.eigh(A)
+    ker = np.abs(ev) < 1e-11 * ev.max()
+    K = V[:, ker]
+    rng = np.random.default_rng(1)
+    b = o.pressure_apply(rng.standard_normal(o.shape)).ravel()
+    x0 = rng.standard_normal(o.ndof)
+    inv = np.where(ker, 0.0, 1.0 / np.where(ker, 1.0, ev))
+    ref = K @ (K.T @ x0) + V @ (inv * (V.T @ b))
+    x = o.pressure_solve_exact(b.reshape(o.shape), x0.reshape(o.shape)).ravel()
+    assert np.linalg.norm(x - ref) <= 1e-12 * np.linalg.norm(ref)
+    # kernel patterns of the oracle span exactly the numerical kernel
+    Kp = o.kernel_patterns()
+    assert Kp.shape[0] == ker.sum()
+    Av = o.dense(o.viscous_apply)
+    bv = rng.standard_normal(o.ndof)
+    xv = o.viscous_solve_exact(bv.reshape(o.shape)).ravel()
+    assert np.linalg.norm(xv - np.linalg.solve(Av, bv)) <= 1e-12 * np.linalg.norm(xv)
+
+
+def test_exact_step_matches_cg_step():
+    """step_exact (both systems solved exactly) equals step with CG run to
+    1e-14 on a small grid."""
+    o = _oracle(2, (6, 5), 3, nu=0.05, theta=0.55, dt=0.01)
+    o.rtol_p = o.rtol_v = 1e-14
+    Us, P = _tg_state(o)
+    U1, P1, _ = o.step(Us, P)
+    U2, P2 = o.step_exact(Us, P)
+    for a, c in zip(U1, U2):
+        assert np.linalg.norm(a - c) <= 1e-11 * np.linalg.norm(c)
+    assert np.linalg.norm(P1 - P2) <= 1e-10 * np.linalg.norm(P2)
