@@ -565,8 +565,9 @@ class Oracle:
         """(M + nu A') x = b solved exactly (block_circulant_solve)."""
         return self.block_circulant_solve(b, b, 1.0, self.nu)
 
-    def step_exact(self, Us, P):
-        """`step` with both linear systems solved exactly instead of by CG."""
+    def step_exact(self, Us, P, intermediates=None):
+        """`step` with both linear systems solved exactly instead of by CG.
+        If `intermediates` is a dict, U* and b are stored in it."""
         V = [self.dual_to_main(Us[d], d) for d in range(self.dim)]
         F = self.rk3(V)
         Vh = [self.viscous_solve_exact(self.mass_all(F[c])) for c in range(self.dim)]
@@ -576,6 +577,9 @@ class Oracle:
         x = self.pressure_solve_exact(b, P)
         Pn = x - self.physical_mean(x)
         q = self.theta * Pn + (1.0 - self.theta) * P
+        if intermediates is not None:
+            intermediates["Ustar"] = Ustar
+            intermediates["b"] = b
         return self.velocity_update(Ustar, q), Pn
 
     # ------------------------------------------------------------- dense assembly

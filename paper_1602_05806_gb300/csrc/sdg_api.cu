@@ -129,6 +129,7 @@ int cg_loop(sdg_handle* h, const Op& op, T* x, T* r, T* const* p, T* Ap, int sid
   int batch = 4;
   const int pk = sizeof(T) == 8 ? 0 : 1;
   int iter_before = h->st_host[sid].iter;
+  long long batches_run = 0;
   for (;;) {
     const bool prof = h->profile != 0;
     const int nb = prof && batch > kProfEvents ? kProfEvents : batch;
@@ -172,6 +173,10 @@ int cg_loop(sdg_handle* h, const Op& op, T* x, T* r, T* const* p, T* Ap, int sid
     iter_before = hs.iter;
     launched = hs.iter;
     if (hs.done || hs.pause) break;
+    if (++batches_run > (long long)h->maxit / 4 + 64) {  // the device caps at maxit; never spin past it
+      set_err("CG host loop ran past maxit without a device stop%s", "");
+      return SDG_ERR_CUDA;
+    }
     if (segment_cap > 0 && hs.iter - iter_start >= segment_cap) break;  // caller replaces the residual
     if (batch < 32) batch *= 2;
   }

@@ -37,6 +37,12 @@ struct Tile {
   static constexpr int LINES = ipow(N1, DIM - 1);
   static constexpr int THREADS = TE * LINES;
   static constexpr int NSLOT = TE + 2 * TY * TZ + 2 * TX * TZ + (DIM == 3 ? 2 * TX * TY : 0);
+  // shared-memory layout of one element: rows of N1 values padded to RS so
+  // that the row-wise (x) and the strided (y, z) line reads of a warp hit
+  // distinct banks
+  static constexpr int RS = N1 + 1;
+  static constexpr int PS = N1 * RS;
+  static constexpr int ES = DIM == 2 ? PS : N1 * PS;
 };
 
 // Stored 1D blocks in the compute precision (see CoefSet): H^C symmetric and
@@ -151,10 +157,12 @@ __global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
   using V = typename std::conditional<VW == 1, T, typename VecOf<T>::V>::type;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* s_in = reinterpret_cast<T*>(smem_raw);  // NSLOT * NPE
-  T* s_out = s_in + NSLOT * NPE;             // TE * NPE
+  constexpr int RS = TS::RS, PS = TS::PS, ES = TS::ES;
+  T* s_in = reinterpret_cast<T*>(smem_raw);  // NSLOT * ES
+  T* s_out = s_in + NSLOT * ES;              // TE * ES
   __shared__ T s_w[N1];
   __shared__ T s_kc[sizeof(T) == 4 ? NPE : 1];
+  __shared__ int s_gel[NSLOT];  // global element held by each slot (-1: unused)
 
   const bool fuse = a.fuse != 0;
   const bool defl = sizeof(T) == 4 && fuse && a.kc != nullptr;
@@ -165,10 +173,6 @@ __global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
     first = (a.st->iter == 0);
     beta = first ? T(0) : T(a.st->rr / a.st->rr_old);
   }
-  if (threadIdx.x < N1) s_w[threadIdx.x] = a.w[threadIdx.x];
-  if (defl)
-    for (int l = threadIdx.x; l < NPE; l += blockDim.x) s_kc[l] = (T)a.kc[l];
-  __syncthreads();
 
   // tile origin and valid extents
   const int bx = blockIdx.x % a.ntile[0];
@@ -179,12 +183,22 @@ __global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
   const int VY = min(TY, a.n[1] - o[1]);
   const int VZ = DIM == 3 ? min(TZ, a.n[2] - o[2]) : 1;
 
-  // ---- stage box + face halo (coalesced, vectorised) ----
+  if (threadIdx.x < N1) s_w[threadIdx.x] = a.w[threadIdx.x];
+  if (defl)
+    for (int l = threadIdx.x; l < NPE; l += blockDim.x) s_kc[l] = (T)a.kc[l];
+  for (int sl = threadIdx.x; sl < NSLOT; sl += blockDim.x) {
+    int g[3];
+    s_gel[sl] = slot_elem<DIM, TX, TY, TZ>(sl, o, VX, VY, VZ, a.n, g)
+                    ? (int)(((long long)g[2] * a.n[1] + g[1]) * a.n[0] + g[0])
+                    : -1;
+  }
+  __syncthreads();
+
+  // ---- stage box + face halo (coalesced vector loads, padded rows) ----
   for (int v = threadIdx.x; v < NSLOT * NV; v += blockDim.x) {
     const int s = v / NV, off = v - s * NV;
-    int g[3];
-    if (!slot_elem<DIM, TX, TY, TZ>(s, o, VX, VY, VZ, a.n, g)) continue;
-    const long long ge = ((long long)g[2] * a.n[1] + g[1]) * a.n[0] + g[0];
+    const int ge = s_gel[s];
+    if (ge < 0) continue;
     const size_t gi = (size_t)ge * NV + off;
     V val;
     if (!fuse) {
@@ -208,7 +222,12 @@ __global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
       }
       if (s < TE) reinterpret_cast<V*>(a.p_out)[gi] = val;
     }
-    reinterpret_cast<V*>(s_in)[s * NV + off] = val;
+    const T* vp = reinterpret_cast<const T*>(&val);
+#pragma unroll
+    for (int k = 0; k < VW; ++k) {
+      const int q = off * VW + k, row = q / N1, l1 = q - row * N1;
+      s_in[s * ES + row * RS + l1] = vp[k];
+    }
   }
   __syncthreads();
 
@@ -221,19 +240,19 @@ __global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
     if (active) {
-      // fixed local indices of this line and its base offset / stride
-      int base, stride;
+      // fixed local indices of this line, its padded base offset and stride
+      int base;
+      const int stride = d == 0 ? 1 : (d == 1 ? RS : PS);
       T wp;
       if (DIM == 2) {
         // d = 0: lam = l2 (row), d = 1: lam = l1 (column)
-        base = d == 0 ? lam * N1 : lam;
-        stride = d == 0 ? 1 : N1;
+        base = d == 0 ? lam * RS : lam;
         wp = s_w[lam];
       } else {
         const int q0 = lam % N1, q1 = lam / N1;
-        if (d == 0) { base = q0 * N1 + q1 * N1 * N1; stride = 1; }
-        else if (d == 1) { base = q0 + q1 * N1 * N1; stride = N1; }
-        else { base = q0 + q1 * N1; stride = N1 * N1; }
+        if (d == 0) base = q0 * RS + q1 * PS;       // (l2, l3) = (q0, q1)
+        else if (d == 1) base = q0 + q1 * PS;       // (l1, l3)
+        else base = q0 + q1 * RS;                   // (l1, l2)
         wp = s_w[q0] * s_w[q1];
       }
       const int sc = (lz * TY + ly) * TX + lx;
@@ -242,9 +261,9 @@ __global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
       T xl[N1], xc[N1], xr[N1];
 #pragma unroll
       for (int k = 0; k < N1; ++k) {
-        xl[k] = s_in[sl * NPE + base + k * stride];
-        xc[k] = s_in[sc * NPE + base + k * stride];
-        xr[k] = s_in[sr * NPE + base + k * stride];
+        xl[k] = s_in[sl * ES + base + k * stride];
+        xc[k] = s_in[sc * ES + base + k * stride];
+        xr[k] = s_in[sr * ES + base + k * stride];
       }
       // Accuracy of the contraction (it matters in FP32).  The operator
       // annihilates every line-repeated pattern q in its local kernel: the
@@ -280,7 +299,7 @@ __global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
         }
       }
       const T f = a.s[d] * wp;
-      T* out = s_out + te * NPE + base;
+      T* out = s_out + te * ES + base;
 #pragma unroll
       for (int m = 0; m < N1; ++m) {
         T acc = T(0);
@@ -298,7 +317,7 @@ __global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
         }
         T val = f * acc;
         if (d == 0) {
-          if (a.cmass != T(0)) val = fma(a.cmass * wp * s_w[m], s_in[sc * NPE + base + m * stride], val);
+          if (a.cmass != T(0)) val = fma(a.cmass * wp * s_w[m], s_in[sc * ES + base + m * stride], val);
           out[m * stride] = val;
         } else {
           out[m * stride] += val;
@@ -312,21 +331,25 @@ __global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
   T dsum = T(0), dcomp = T(0);  // compensated per-thread sum in T
   for (int v = threadIdx.x; v < TE * NV; v += blockDim.x) {
     const int e = v / NV, off = v - e * NV;
-    const int ex = e % TX, ey = (e / TX) % TY, ez = e / (TX * TY);
-    if (ex >= VX || ey >= VY || ez >= VZ) continue;
-    const long long ge = ((long long)(o[2] + ez) * a.n[1] + (o[1] + ey)) * a.n[0] + (o[0] + ex);
-    const V yv = reinterpret_cast<const V*>(s_out)[e * NV + off];
+    const int ge = s_gel[e];
+    if (ge < 0) continue;
+    V yv, pv;
+    T* yp = reinterpret_cast<T*>(&yv);
+    T* pp = reinterpret_cast<T*>(&pv);
+#pragma unroll
+    for (int k = 0; k < VW; ++k) {
+      const int q = off * VW + k, row = q / N1, l1 = q - row * N1;
+      yp[k] = s_out[e * ES + row * RS + l1];
+      pp[k] = s_in[e * ES + row * RS + l1];
+    }
     reinterpret_cast<V*>(a.y)[(size_t)ge * NV + off] = yv;
     if (fuse) {
-      const V pv = reinterpret_cast<const V*>(s_in)[e * NV + off];
-      const T* yp = reinterpret_cast<const T*>(&yv);
-      const T* pp = reinterpret_cast<const T*>(&pv);
 #pragma unroll
       for (int k = 0; k < VW; ++k) {
         const T yk = fma(pp[k], yp[k], -dcomp);
-        const T t = dsum + yk;
-        dcomp = (t - dsum) - yk;
-        dsum = t;
+        const T tt = dsum + yk;
+        dcomp = (tt - dsum) - yk;
+        dsum = tt;
       }
     }
   }
@@ -386,7 +409,7 @@ cudaError_t launch_apply_acc(const sdg_handle* h, const ApplyArgs<T>& in, cudaSt
   p.kc = in.kc;
   const long long nblk = (long long)p.ntile[0] * p.ntile[1] * p.ntile[2];
   if (nblk > h->max_blocks) return cudaErrorInvalidConfiguration;
-  const size_t smem = (size_t)(TS::NSLOT + TS::TE) * TS::NPE * sizeof(T);
+  const size_t smem = (size_t)(TS::NSLOT + TS::TE) * TS::ES * sizeof(T);
   static bool attr_set = false;  // per instantiation; smem need is fixed
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_apply<T, DIM, N1, ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
