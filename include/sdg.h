@@ -235,6 +235,36 @@ int sdg_counters(const sdg_handle* h, long long* launches, double* apply_ms,
 int sdg_diagnostics(sdg_handle* h, double* kinetic_energy, double* div_norm,
                     void* stream);
 
+/* ---------------------------------------------------------------- allocation-free */
+
+/* Kinetic energy K = (1/|Omega|) int |v|^2 / 2 of caller-owned velocity
+ * arrays, like the kinetic_energy output of sdg_diagnostics, for callers that
+ * cannot allocate device memory: code recording a CUDA graph (an allocation
+ * while a stream is captured is an error), code whose device memory is owned
+ * by another allocator or pool, and latency-critical loops where an
+ * allocation would stall the device.  The paper has no counterpart; it is a
+ * service of this library.
+ *   - Needs no handle and calls no cudaMalloc, cudaFree or allocating
+ *     library routine.  Its scratch (partial sums and a ticket counter) is a
+ *     fixed 32 KB array compiled into the library, held by every GPU that
+ *     loads it until the process exits.
+ *   - grid, N: as for sdg_create (periodic box, 0 <= N <= 11).  u, v (, w in
+ *     3D, ignored in 2D): device arrays of ncell * (N+1)^dim doubles in the
+ *     layout above, each component on its own grid.  ke: device pointer to
+ *     one double, written on `stream`.
+ *   - At most 67,108,864 nodes per component; larger grids return
+ *     SDG_ERR_INVALID_ARG with the limit in sdg_last_error.
+ *   - The first call on a device looks up the scratch array's device
+ *     address (cudaGetSymbolAddress) with that device current; make that
+ *     first call before any stream capture.
+ *   - Every call shares the one scratch array: calls that can overlap on the
+ *     GPU (different streams, or different host threads) race and must be
+ *     ordered by the caller.  Each call clears the counter it relies on.
+ * Errors: INVALID_ARG, CUDA. */
+int sdg_kinetic_energy_noalloc(const sdg_grid* grid, int N, const double* u,
+                               const double* v, const double* w, double* ke,
+                               void* stream);
+
 const char* sdg_strerror(int status);
 const char* sdg_last_error(void);
 

@@ -66,6 +66,8 @@ Op viscous_op(const sdg_handle* h) {
 
 namespace sdg {
 
+void set_last_error(const char* msg) { std::snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 cudaError_t launch_apply_f64(const sdg_handle* h, const ApplyArgs<double>& a, cudaStream_t s) {
   return h->dim == 2 ? apply_dispatch_2d(h, a, s) : apply_dispatch_3d(h, a, s);
 }

@@ -120,6 +120,9 @@ struct sdg_handle {
 
 namespace sdg {
 
+// Record the text returned by sdg_last_error (this thread).
+void set_last_error(const char* msg);
+
 // ---- launchers (sdg_apply_*.cu) -------------------------------------------
 // y = cmass * W x + sum_d s[d] M^{perp d} (H^L x_{i-1} + H^C x_i + H^R x_{i+1})_d
 // If fuse != 0: the input is p = r + beta p_old (beta from `st`, p = r on the

@@ -32,7 +32,7 @@ EXPORTS = (
     "sdg_pressure_apply", "sdg_viscous_apply", "sdg_pressure_cg", "sdg_viscous_cg",
     "sdg_dual_to_main", "sdg_main_to_dual", "sdg_convect", "sdg_pressure_rhs",
     "sdg_velocity_update", "sdg_step", "sdg_set_profiling", "sdg_counters", "sdg_diagnostics",
-    "sdg_strerror", "sdg_last_error",
+    "sdg_kinetic_energy_noalloc", "sdg_strerror", "sdg_last_error",
 )
 
 
@@ -98,6 +98,7 @@ def lib():
         L.sdg_set_profiling.argtypes = [vp, ip]
         L.sdg_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), dp,
                                    ctypes.POINTER(ctypes.c_longlong)]
+        L.sdg_kinetic_energy_noalloc.argtypes = [ctypes.POINTER(sdg_grid), ip, vp, vp, vp, vp, vp]
         L.sdg_strerror.argtypes = [ip]
         L.sdg_strerror.restype = ctypes.c_char_p
         L.sdg_last_error.restype = ctypes.c_char_p
@@ -162,6 +163,19 @@ def sdg_kernel_projector(N):
     d = ctypes.c_int()
     check(lib().sdg_kernel_projector(N, P.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(d)))
     return P.reshape(N + 1, N + 1), d.value
+
+
+def sdg_kinetic_energy_noalloc(dim, n, L, N, U, ke, stream=None):
+    """Kinetic energy of device velocity arrays U (dim tensors) into the
+    one-element device tensor `ke`, without any device allocation."""
+    g = sdg_grid()
+    g.dim = dim
+    for d in range(3):
+        g.n[d] = int(n[d]) if d < dim else 1
+        g.L[d] = float(L[d]) if d < dim else 1.0
+    w = U[2] if dim == 3 else None
+    check(lib().sdg_kinetic_energy_noalloc(ctypes.byref(g), int(N), _ptr(U[0]), _ptr(U[1]), _ptr(w),
+                                           _ptr(ke), _stream(stream)))
 
 
 class Handle:
