@@ -171,7 +171,8 @@ __global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
   if (fuse) {
     if (a.st->done || a.st->pause) return;  // uniform: written by the previous kernel
     first = (a.st->iter == 0);
-    beta = first ? T(0) : T(a.st->rr / a.st->rr_old);
+    // beta was formed once by the previous kernel (no FP64 division per thread)
+    if (!first) beta = sizeof(T) == 4 ? (T)a.st->beta_f : (T)a.st->beta;
   }
 
   // tile origin and valid extents
@@ -354,8 +355,16 @@ __global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
     }
   }
   if (fuse) {
-    double v1[1] = {(double)dsum - (double)dcomp}, tot[1];
-    if (grid_sum<1>(v1, a.partials, &a.st->counter, tot)) {
+    double tot[1];
+    bool last;
+    if constexpr (sizeof(T) == 4) {
+      F2 v1[1] = {F2{(float)dsum, -(float)dcomp}};
+      last = grid_sum_f2<1>(v1, a.partials, &a.st->counter, tot);
+    } else {
+      double v1[1] = {(double)dsum - (double)dcomp};
+      last = grid_sum<1>(v1, a.partials, &a.st->counter, tot);
+    }
+    if (last) {
       if (threadIdx.x == 0) {
         SolverState* st = a.st;
         const double pAp = tot[0];
@@ -367,6 +376,7 @@ __global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
         } else {
           st->alpha = st->rr / pAp;
         }
+        st->alpha_f = (float)st->alpha;
       }
     }
   }

@@ -68,6 +68,86 @@ __device__ __forceinline__ bool grid_sum(double (&v)[K], double* partials, unsig
   return true;
 }
 
+// ---- FP32 reductions without FP64 arithmetic per thread -------------------
+// GB300 issues FP64 at 1/64 of the FP32 rate, so FP32 kernels reduce their
+// dot products as unevaluated float pairs (hi + lo) with the error-free
+// TwoSum addition; FP64 is used only to add the per-warp pairs of a block.
+struct F2 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb);
+  return F2{s, a.lo + b.lo + e};
+}
+
+// Sum K float pairs over the block; totals (as doubles) in every thread.
+template <int K>
+__device__ __forceinline__ void block_sum_f2(F2 (&v)[K], double* s_red, double (&out)[K]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    F2 t = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      F2 u{__shfl_xor_sync(0xffffffffu, t.hi, o), __shfl_xor_sync(0xffffffffu, t.lo, o)};
+      t = f2_add(t, u);
+    }
+    if (lane == 0) s_red[k * 32 + wid] = (double)t.hi + (double)t.lo;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double a = 0.0;
+      for (int w = 0; w < nw; ++w) a += s_red[k * 32 + w];
+      s_red[k * 32] = a;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) out[k] = s_red[k * 32];
+  __syncthreads();
+}
+
+// grid_sum for float pairs: per-block totals in FP64, same deterministic
+// last-block finish as grid_sum.
+template <int K>
+__device__ __forceinline__ bool grid_sum_f2(F2 (&v)[K], double* partials, unsigned int* counter,
+                                            double (&tot)[K]) {
+  static_assert(K <= kPartialSlots, "too many reduction slots");
+  __shared__ double s_red2[32 * K];
+  __shared__ int s_last2;
+  double b[K];
+  block_sum_f2<K>(v, s_red2, b);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) partials[(size_t)blockIdx.x * kPartialSlots + k] = b[k];
+    __threadfence();
+    unsigned int t = atomicAdd(counter, 1u);
+    s_last2 = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last2) return false;
+  __threadfence();
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.0;
+  for (unsigned int i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] += __ldcg(&partials[(size_t)i * kPartialSlots + k]);
+  }
+  double u[K];
+  block_sum<K>(acc, s_red2, u);
+#pragma unroll
+  for (int k = 0; k < K; ++k) tot[k] = u[k];
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
 // ---- layout ----------------------------------------------------------------
 __device__ __forceinline__ void split_index(const Geo& g, long long idx, int e[3], int l[3]) {
   const long long el = idx / g.npe;

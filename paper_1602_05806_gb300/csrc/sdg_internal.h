@@ -18,7 +18,9 @@ struct SolverState {
   double rr;        // current ||r||^2 (recursive)
   double rr_old;    // previous ||r||^2
   double pAp;       // p^T A p of the current iteration
-  double alpha;     // rr / pAp
+  double alpha;     // rr / pAp (set by the operator kernel's last block)
+  double beta;      // rr / rr_old (set by the update kernel's last block)
+  float alpha_f, beta_f;  // the same in FP32, read by every thread of FP32 kernels
   double bnorm2;    // ||b||^2
   double tol2;      // (rtol ||b||)^2
   double mean;      // mixed: mean of the FP64 residual (removed: periodic kernel)

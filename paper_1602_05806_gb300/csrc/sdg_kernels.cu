@@ -53,6 +53,9 @@ __global__ void __launch_bounds__(kThreads)
     st->maxit = maxit;
     st->status = SDG_OK;
     st->alpha = 0.0;
+    st->beta = 0.0;
+    st->alpha_f = 0.0f;
+    st->beta_f = 0.0f;
     st->pAp = 0.0;
     st->reliable = 0;
     st->pause = 0;
@@ -93,6 +96,7 @@ struct DotAcc<float> {
     s = t;
   }
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+  __device__ __forceinline__ F2 pair() const { return F2{s, -c}; }
 };
 
 template <typename T>
@@ -110,7 +114,7 @@ __global__ void __launch_bounds__(kThreads)
     k_cg_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ Ap,
                 long long n, SolverState* st, double* partials, Deflate df) {
   if (st->done || st->pause) return;
-  extern __shared__ double s_dyn[];
+  extern __shared__ double s_dyn[];  // (deflation only)
   float* s_k = reinterpret_cast<float*>(s_dyn);  // npe floats (deflation)
   const bool defl = df.kpart != nullptr;
   if (defl) {
@@ -119,7 +123,7 @@ __global__ void __launch_bounds__(kThreads)
   }
   using V = typename V4<T>::V;
   constexpr int W = V4<T>::W;
-  const T alpha = (T)st->alpha;
+  const T alpha = sizeof(T) == 4 ? (T)st->alpha_f : (T)st->alpha;
   DotAcc<T> rr;
   const long long nv = n / W;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -155,8 +159,16 @@ __global__ void __launch_bounds__(kThreads)
       df.kpart[(size_t)blockIdx.x * df.npe + l] = s_k[l];
     __threadfence();
   }
-  double v[1] = {rr.value()}, tot[1];
-  if (grid_sum<1>(v, partials, &st->counter, tot)) {
+  double tot[1];
+  bool last;
+  if constexpr (sizeof(T) == 4) {
+    F2 v[1] = {rr.pair()};
+    last = grid_sum_f2<1>(v, partials, &st->counter, tot);
+  } else {
+    double v[1] = {rr.value()};
+    last = grid_sum<1>(v, partials, &st->counter, tot);
+  }
+  if (last) {
     double rK2 = 0.0;
     if (defl) {
       // S[l] = sum over blocks of the partial sums, in FP64, by G thread groups
@@ -206,6 +218,8 @@ __global__ void __launch_bounds__(kThreads)
       if (rr < 0.0) rr = 0.0;
       st->rr_old = st->rr;
       st->rr = rr;
+      st->beta = st->rr_old > 0.0 ? rr / st->rr_old : 0.0;  // for the next direction
+      st->beta_f = (float)st->beta;
       st->iter += 1;
       if (rr > st->maxrr) st->maxrr = rr;
       if (!isfinite(rr)) {
@@ -277,6 +291,9 @@ __global__ void __launch_bounds__(kThreads)
     }
     const double rr = rrp * st->sigma * st->sigma;
     st->mean = mean;
+    // the next direction: p = r_true + (rr_true / rr_old) p_old
+    st->beta = (!init && st->rr_old > 0.0) ? rr / st->rr_old : 0.0;
+    st->beta_f = (float)st->beta;
     // the next direction uses beta = rr_true / rr_k, rr_k being the residual
     // norm of the iteration before the one that triggered the update
     if (init) st->rr_old = rr;
