@@ -136,7 +136,7 @@ def oracle_sample_pressure_solve(cells=CPU_SAMPLE_CELLS):
     and viscous solves (not timed).  Returns (GDOF/s, seconds, dof, applies)."""
     from oracle import Grid, Oracle, cg
     import sdg_inputs as si
-    from paper_1602_05806_gb300.workloads import WORKLOADS
+    from paper_1602_05806_gb300.workloads import WORKLOADS, cfl_number, convection_substeps
     w = WORKLOADS[WORKLOAD]
     L = (2 * math.pi,) * 2
     o = Oracle(Grid(2, cells, L), w["N"], w["nu"], w["theta"], w["dt"])
@@ -146,6 +146,8 @@ def oracle_sample_pressure_solve(cells=CPU_SAMPLE_CELLS):
     for d in range(2):
         x, y = o.coords(d)
         U.append(si.taylor_green_2d(x, y)[d] + si.perturbation_velocity(modes, x, y)[d])
+    cfl = cfl_number(2, cells, L, w["N"], w["dt"], [float(np.abs(u).max()) for u in U])
+    o.nsub = convection_substeps(cfl) if cfl >= 1.0 else 1
     x, y = o.coords(None)
     P = si.taylor_green_2d(x, y)[2]
     P = P - o.physical_mean(P)
@@ -215,6 +217,7 @@ def run_ours(args):
     w, U0, P0 = workload_state(WORKLOAD)
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
     h = sdg.Handle(2, w["n"], w["L"], w["N"], w["nu"], w["theta"], w["dt"])
+    h.set_convection_substeps(w["nsub"])
     ndof = h.ndof
     h.set_options(sdg.SDG_MIXED, 1e-12, 1e-12)
     h.set_state([dev(u) for u in U0], dev(P0))
@@ -375,6 +378,7 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "dim": 2, "cells": list(w["n"]), "N": w["N"],
                            "dof": ndof, "nu": w["nu"], "theta": w["theta"], "dt": w["dt"],
+                           "cfl": round(w["cfl"], 3), "convection_substeps": w["nsub"],
                            "rtol": 1e-12, "precision": "FP32 CG, FP64 reliable updates",
                            "l2": "512 MB buffer written between timed steps (outside the step events)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

@@ -131,6 +131,14 @@ int sdg_set_options(sdg_handle* h, int precision, double rtol_p, double rtol_v,
  * operator kernel already annihilates those patterns exactly). */
 int sdg_set_mixed_options(sdg_handle* h, double delta, int max_updates, int deflate);
 
+/* Number of equal SSP-RK3 sub-steps (dt / nsub each) in which the explicit
+ * convection of Sec. 2.2 advances over one time step; the pressure and
+ * viscous solves still take the full dt.  The explicit stage is stable only
+ * below the CFL limit of Eq. CFL1 (CFL < 1); a time step above it stays
+ * stable with nsub >= CFL / 0.5.  nsub = 1 (default) is the scheme as the
+ * paper states it.  Errors: INVALID_ARG unless 1 <= nsub <= 1000. */
+int sdg_set_convection_substeps(sdg_handle* h, int nsub);
+
 /* Number of DOF of one field (ncell * n1^dim). */
 long long sdg_ndof(const sdg_handle* h);
 
@@ -186,7 +194,8 @@ int sdg_main_to_dual(sdg_handle* h, int d, const double* in, double* out,
 
 /* Explicit convection of a main-grid velocity V (dim device arrays) over one
  * dt by third-order SSP Runge-Kutta with the Rusanov-flux DG operator
- * (Eqs. Fu-Fw, Sec. 2.2); writes F (dim device arrays). */
+ * (Eqs. Fu-Fw, Sec. 2.2), in sdg_set_convection_substeps sub-steps; writes
+ * F (dim device arrays, disjoint from V). */
 int sdg_convect(sdg_handle* h, const double* const* V, double* const* F,
                 void* stream);
 

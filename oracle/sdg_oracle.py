@@ -34,6 +34,10 @@ Readings of points the paper leaves open (each is exercised by a test):
   R10 initial data: point values at the element's own GL nodes.
   R11 CG: Hestenes-Stiefel, Euclidean norm, stop on the recursive residual
       ||r_k|| <= rtol ||b||, x0 = P^n (pressure) / Fu (viscous).
+  R12 a time step above the explicit limit of Eq. CFL1 (CFL >= 1) keeps its
+      dt for the implicit solves and advances the explicit convection in
+      nsub equal SSP-RK3 sub-steps of dt / nsub (nsub = 1: the scheme as
+      stated; otherwise nsub >= CFL / 0.5).
 """
 from __future__ import annotations
 
@@ -226,7 +230,8 @@ class Oracle:
     """
 
     def __init__(self, grid: Grid, N: int, nu: float, theta: float, dt: float,
-                 rtol_p: float = 1e-12, rtol_v: float = 1e-12, maxit: int = 20000):
+                 rtol_p: float = 1e-12, rtol_v: float = 1e-12, maxit: int = 20000,
+                 nsub: int = 1):
         if grid.dim not in (2, 3):
             raise ValueError("dim must be 2 or 3")
         self.g = grid
@@ -235,6 +240,9 @@ class Oracle:
         self.n1 = N + 1
         self.nu, self.theta, self.dt = float(nu), float(theta), float(dt)
         self.rtol_p, self.rtol_v, self.maxit = rtol_p, rtol_v, maxit
+        if int(nsub) < 1:
+            raise ValueError("nsub must be >= 1")
+        self.nsub = int(nsub)
         self.B = Basis(N)
 
     # ------------------------------------------------------------- layout
@@ -407,14 +415,17 @@ class Oracle:
         return out
 
     def rk3(self, V):
-        """Third-order SSP Runge-Kutta (Shu-Osher form) on dV/dt = L(V) (reading R9)."""
-        dt = self.dt
-        L0 = self.convection(V)
-        V1 = [V[c] + dt * L0[c] for c in range(self.dim)]
-        L1 = self.convection(V1)
-        V2 = [0.75 * V[c] + 0.25 * (V1[c] + dt * L1[c]) for c in range(self.dim)]
-        L2 = self.convection(V2)
-        return [V[c] / 3.0 + (2.0 / 3.0) * (V2[c] + dt * L2[c]) for c in range(self.dim)]
+        """Third-order SSP Runge-Kutta (Shu-Osher form) on dV/dt = L(V) over one
+        dt (reading R9), taken in nsub equal sub-steps (reading R12)."""
+        k = self.dt / self.nsub
+        for _ in range(self.nsub):
+            L0 = self.convection(V)
+            V1 = [V[c] + k * L0[c] for c in range(self.dim)]
+            L1 = self.convection(V1)
+            V2 = [0.75 * V[c] + 0.25 * (V1[c] + k * L1[c]) for c in range(self.dim)]
+            L2 = self.convection(V2)
+            V = [V[c] / 3.0 + (2.0 / 3.0) * (V2[c] + k * L2[c]) for c in range(self.dim)]
+        return V
 
     # ------------------------------------------------------------- gauge (reading R3)
     def physical_mean(self, P):

@@ -417,6 +417,7 @@ int sdg_create(const sdg_grid* grid, int N, double nu, double theta, double dt, 
   h->precision = SDG_FP64;
   h->rtol_p = h->rtol_v = 1e-12;
   h->delta = 0.1;
+  h->nsub = 1;
   h->maxit = 1000000;
   h->max_updates = 1000;
   build_basis(N, &h->basis);
@@ -561,6 +562,13 @@ int sdg_set_mixed_options(sdg_handle* h, double delta, int max_updates, int defl
   return SDG_OK;
 }
 
+int sdg_set_convection_substeps(sdg_handle* h, int nsub) {
+  SDG_ARG(h, "NULL handle");
+  SDG_ARG(nsub >= 1 && nsub <= 1000, "nsub must be in [1, 1000]");
+  h->nsub = nsub;
+  return SDG_OK;
+}
+
 long long sdg_ndof(const sdg_handle* h) { return h ? h->g.ndof : 0; }
 
 int sdg_set_state(sdg_handle* h, const double* u, const double* v, const double* w, const double* p,
@@ -630,14 +638,25 @@ int sdg_main_to_dual(sdg_handle* h, int d, const double* in, double* out, void* 
   return SDG_OK;
 }
 
+// SSP-RK3 (Shu-Osher form) of the explicit convection over one dt, in
+// h->nsub equal sub-steps: W <- W/3 + 2/3 (W2 + k L(W2)) with
+// W1 = W + k L(W), W2 = 3/4 W + 1/4 (W1 + k L(W1)), k = dt / nsub.  The first
+// sub-step reads V; later ones update F in place (out may alias V0).
+static int convect_rk3(sdg_handle* h, const double* const* V, double* const* F, cudaStream_t s) {
+  const double k = h->dt / h->nsub;
+  for (int sub = 0; sub < h->nsub; ++sub) {
+    const double* const* W = sub == 0 ? V : F;
+    SDG_K(k_convect_stage(h, nullptr, W, h->S1, 0.0, 1.0, k, s));
+    SDG_K(k_convect_stage(h, W, h->S1, h->S2, 0.75, 0.25, k, s));
+    SDG_K(k_convect_stage(h, W, h->S2, F, 1.0 / 3.0, 2.0 / 3.0, k, s));
+  }
+  return SDG_OK;
+}
+
 int sdg_convect(sdg_handle* h, const double* const* V, double* const* F, void* stream) {
   SDG_ARG(h && V && F, "bad arguments");
   for (int d = 0; d < h->dim; ++d) SDG_ARG(V[d] && F[d], "NULL component");
-  cudaStream_t s = S(stream);
-  SDG_K(k_convect_stage(h, nullptr, V, h->S1, 0.0, 1.0, s));
-  SDG_K(k_convect_stage(h, V, h->S1, h->S2, 0.75, 0.25, s));
-  SDG_K(k_convect_stage(h, V, h->S2, F, 1.0 / 3.0, 2.0 / 3.0, s));
-  return SDG_OK;
+  return convect_rk3(h, V, F, S(stream));
 }
 
 int sdg_pressure_rhs(sdg_handle* h, const double* const* Ustar, const double* P_old, double* b, void* stream) {
@@ -666,9 +685,10 @@ int sdg_step(sdg_handle* h, int nsteps, sdg_step_info* info, void* stream) {
     // 1. dual -> main (Eq. l2forward)
     for (int d = 0; d < h->dim; ++d) SDG_K(k_dual_to_main(h, d, h->U[d], h->Vm[d], s));
     // 2. SSP-RK3 of the explicit convection (Eqs. Fu-Fw)
-    SDG_K(k_convect_stage(h, nullptr, h->Vm, h->S1, 0.0, 1.0, s));
-    SDG_K(k_convect_stage(h, h->Vm, h->S1, h->S2, 0.75, 0.25, s));
-    SDG_K(k_convect_stage(h, h->Vm, h->S2, h->F, 1.0 / 3.0, 2.0 / 3.0, s));
+    {
+      const int rc = convect_rk3(h, h->Vm, h->F, s);
+      if (rc != SDG_OK) return rc;
+    }
     // 3. implicit viscosity per component (Eq. LOdiffusionU-W)
     for (int c = 0; c < h->dim; ++c) {
       SDG_K(k_mass_rhs(h, h->F[c], h->b, h->Vh[c], s));

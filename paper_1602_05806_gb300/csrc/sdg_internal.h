@@ -69,6 +69,7 @@ struct sdg_handle {
   int dim;
   double L[3], dx[3];
   double nu, theta, dt;
+  int nsub;                      // SSP-RK3 sub-steps of the explicit convection per dt
   int precision;
   double rtol_p, rtol_v;
   double delta;     // mixed: reliable-update factor
@@ -201,9 +202,10 @@ cudaError_t kernel_restore(const sdg_handle* h, double* x, const double* x0, cud
 // step stages
 cudaError_t k_dual_to_main(const sdg_handle* h, int d, const double* in, double* out, cudaStream_t s);
 cudaError_t k_main_to_dual(const sdg_handle* h, int d, const double* in, double* out, cudaStream_t s);
-// out_c = a * V0_c + b * (V_c + dt L(V)_c) for every component c
+// out_c = a * V0_c + b * (V_c + dt L(V)_c) for every component c (out may
+// alias V0, not V)
 cudaError_t k_convect_stage(const sdg_handle* h, const double* const* V0, const double* const* V,
-                            double* const* out, double a, double b, cudaStream_t s);
+                            double* const* out, double a, double b, double dt, cudaStream_t s);
 // b = W F, x0 = F
 cudaError_t k_mass_rhs(const sdg_handle* h, const double* F, double* b, double* x0, cudaStream_t s);
 // out = base + scale * sum_d (1/dx_d) M^{perp d} (Rb U_d - Lb U_d,shift)  ; reduces sum(out) into st->red[0]

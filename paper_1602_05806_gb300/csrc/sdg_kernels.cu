@@ -724,7 +724,7 @@ cudaError_t k_main_to_dual(const sdg_handle* h, int d, const double* in, double*
   return cudaGetLastError();
 }
 cudaError_t k_convect_stage(const sdg_handle* h, const double* const* V0, const double* const* V,
-                            double* const* out, double a, double b, cudaStream_t s) {
+                            double* const* out, double a, double b, double dt, cudaStream_t s) {
   ConvectParams p;
   p.g = h->g;
   for (int d = 0; d < 3; ++d) {
@@ -735,7 +735,7 @@ cudaError_t k_convect_stage(const sdg_handle* h, const double* const* V0, const 
   }
   p.a = a;
   p.b = b;
-  p.dt = h->dt;
+  p.dt = dt;
   k_convect<<<grid_full(h->g.ndof), kThreads, 0, s>>>(p, h->mats);
   return cudaGetLastError();
 }

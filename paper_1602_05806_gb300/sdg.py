@@ -28,7 +28,7 @@ SDG_MIXED = 1
 # every symbol include/sdg.h declares
 EXPORTS = (
     "sdg_nodes", "sdg_matrices", "sdg_kernel_projector", "sdg_create", "sdg_destroy", "sdg_set_options",
-    "sdg_set_mixed_options", "sdg_ndof", "sdg_set_state", "sdg_get_state",
+    "sdg_set_mixed_options", "sdg_set_convection_substeps", "sdg_ndof", "sdg_set_state", "sdg_get_state",
     "sdg_pressure_apply", "sdg_viscous_apply", "sdg_pressure_cg", "sdg_viscous_cg",
     "sdg_dual_to_main", "sdg_main_to_dual", "sdg_convect", "sdg_pressure_rhs",
     "sdg_velocity_update", "sdg_step", "sdg_set_profiling", "sdg_counters", "sdg_diagnostics",
@@ -80,6 +80,7 @@ def lib():
         L.sdg_destroy.argtypes = [vp]
         L.sdg_set_options.argtypes = [vp, ip, ctypes.c_double, ctypes.c_double, ip]
         L.sdg_set_mixed_options.argtypes = [vp, ctypes.c_double, ip, ip]
+        L.sdg_set_convection_substeps.argtypes = [vp, ip]
         L.sdg_ndof.argtypes = [vp]
         L.sdg_ndof.restype = ctypes.c_longlong
         L.sdg_set_state.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -214,6 +215,10 @@ class Handle:
 
     def set_mixed_options(self, delta=0.1, max_updates=1000, deflate=False):
         check(lib().sdg_set_mixed_options(self.h, delta, max_updates, 1 if deflate else 0))
+
+    def set_convection_substeps(self, nsub):
+        """SSP-RK3 sub-steps of the explicit convection per time step."""
+        check(lib().sdg_set_convection_substeps(self.h, int(nsub)))
 
     def set_profiling(self, enable=True):
         check(lib().sdg_set_profiling(self.h, 1 if enable else 0))

@@ -78,8 +78,22 @@ WORKLOADS = {
 }
 
 
+def cfl_number(dim, n, L, N, dt, umax):
+    """CFL number of a time step dt by Eq. CFL1:
+    dt (2N+1) sum_d umax_d / dx_d, umax_d the largest |u_d|."""
+    return dt * (2 * N + 1) * sum(umax[d] * n[d] / L[d] for d in range(dim))
+
+
+def convection_substeps(cfl, target=0.5):
+    """SSP-RK3 sub-steps that bring the explicit convection to CFL <= target."""
+    return max(1, int(math.ceil(cfl / target - 1e-12)))
+
+
 def workload_state(name, n_override=None):
-    """(params, U, P) of a named workload; `n_override` shrinks the grid."""
+    """(params, U, P) of a named workload; `n_override` shrinks the grid.
+    params gains "L", "cfl" (Eq. CFL1 from the initial velocity) and "nsub"
+    (convection sub-steps per dt that keep each explicit sub-step at
+    CFL <= 0.5; 1 when dt is within the limit)."""
     w = dict(WORKLOADS[name])
     if n_override is not None:
         w["n"] = tuple(n_override)
@@ -91,4 +105,7 @@ def workload_state(name, n_override=None):
         modes = si.stream_modes(m["seed"], m["nmodes"], m["kmax"], m["amplitude"])
     U, P = taylor_green_state(dim, w["n"], L, w["N"], modes=modes)
     w["L"] = L
+    umax = [float(np.abs(u).max()) for u in U]
+    w["cfl"] = cfl_number(dim, w["n"], L, w["N"], w["dt"], umax)
+    w["nsub"] = convection_substeps(w["cfl"]) if w["cfl"] >= 1.0 else 1
     return w, U, P

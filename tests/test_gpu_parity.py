@@ -183,6 +183,13 @@ def test_stages(dim, n, N):
     ref = o.rk3(V)
     for c in range(dim):
         assert rel(host(out[c]), ref[c]) <= 1e-13
+    # the same dt in three sub-steps (reading R12)
+    h.set_convection_substeps(3)
+    o.nsub = 3
+    h.convect([dev(v) for v in V], out)
+    ref = o.rk3(V)
+    for c in range(dim):
+        assert rel(host(out[c]), ref[c]) <= 1e-13
     # pressure right-hand side and velocity update
     P = rng.standard_normal(o.shape)
     b = torch.empty_like(D[0])
@@ -265,11 +272,41 @@ def test_step_parity_3d_ragged(precision):
         assert rel(host(Po), P) <= tol
 
 
+@pytest.mark.parametrize("precision", [sdg.SDG_FP64, sdg.SDG_MIXED])
+def test_step_parity_above_cfl_limit(precision):
+    """Perturbed Taylor-Green on 8x8 cells, N=7, dt=0.064: CFL 2.44 by
+    Eq. CFL1, run with five convection sub-steps per dt; four steps compared
+    with the oracle after each."""
+    o, h = make(2, (8, 8), 7, nu=1e-3, theta=0.51, dt=0.064)
+    o.rtol_p = o.rtol_v = 1e-13
+    o.nsub = 5
+    h.set_convection_substeps(5)
+    h.set_options(precision, 1e-13, 1e-13, 1000000)
+    modes = si.stream_modes(0, 32, 8, 1e-2)
+    U, P = _oracle_tg(o, modes)
+    Ug, Pg = taylor_green_state(2, (8, 8), (TWO_PI, TWO_PI), 7, modes=modes)
+    h.set_state([dev(u) for u in Ug], dev(Pg))
+    tol = 1e-11 if precision == sdg.SDG_FP64 else 1e-10
+    Uo = [torch.empty(o.shape, dtype=torch.float64, device="cuda") for _ in range(2)]
+    Po = torch.empty(o.shape, dtype=torch.float64, device="cuda")
+    for step in range(4):
+        U, P, _ = o.step(U, P)
+        assert h.step(1)["status"] == sdg.SDG_OK
+        h.get_state(Uo, Po)
+        for d in range(2):
+            e = rel(host(Uo[d]), U[d])
+            assert e <= tol, (step, d, e)
+        e = rel(host(Po), P)
+        assert e <= 1e-10, (step, e)
+
+
 def test_step_parity_perturbed_64x64_N5_reduced():
     """The 64x64, N=5 perturbed workload on a 12x10 grid (same degree,
     viscosity, time step and perturbation), three steps."""
     w, Ug, Pg = workload_state("tg2d_64x64_N5", n_override=(12, 10))
     o, h = make(2, w["n"], w["N"], nu=w["nu"], theta=w["theta"], dt=w["dt"])
+    o.nsub = w["nsub"]
+    h.set_convection_substeps(w["nsub"])
     o.rtol_p = o.rtol_v = 1e-13
     h.set_options(sdg.SDG_FP64, 1e-13, 1e-13, 1000000)
     m = w["modes"]
@@ -312,7 +349,10 @@ def test_full_size_step_256x256_N7(precision):
     rtol 1e-12 on this system, cond ~1e7, carries pressure errors of order
     1e-10 in its smoothest modes)."""
     w, Ug, Pg = workload_state("tg2d_256x256_N7")
+    assert w["nsub"] == 5  # CFL 2.47 by Eq. CFL1
     o, h = make(2, w["n"], w["N"], nu=w["nu"], theta=w["theta"], dt=w["dt"])
+    o.nsub = w["nsub"]
+    h.set_convection_substeps(w["nsub"])
     h.set_options(precision, 1e-12, 1e-12, 1000000)
     h.set_state([dev(u) for u in Ug], dev(Pg))
     info = h.step(1)

@@ -383,6 +383,50 @@ def test_rk3_coefficients(monkeypatch):
     assert np.allclose(out[0], g) and np.allclose(out[1], 2 * g)
 
 
+@pytest.mark.parametrize("nsub", [2, 5])
+def test_rk3_substeps(monkeypatch, nsub):
+    """Reading R12: nsub sub-steps of length dt / nsub.  On dV/dt = lambda V
+    the result is the cubic Taylor factor of z / nsub raised to nsub."""
+    o = _oracle(2, (2, 2), 1, dt=0.9)
+    o.nsub = nsub
+    lam = -2.3
+    monkeypatch.setattr(o, "convection", lambda V: [lam * x for x in V])
+    V = [np.ones(o.shape), -np.ones(o.shape)]
+    out = o.rk3(V)
+    z = lam * o.dt / nsub
+    g = (1 + z + z * z / 2 + z**3 / 6) ** nsub
+    assert np.allclose(out[0], g, rtol=1e-14) and np.allclose(out[1], -g, rtol=1e-14)
+
+
+def test_subcycling_above_cfl_limit():
+    """Eq. CFL1 bounds the explicit convection to CFL < 1.  The perturbed
+    Taylor-Green field at CFL 2.44 (8x8 cells, N=7, dt=0.064) blows up within
+    a few steps with one RK3 step per dt, and decays smoothly with five
+    sub-steps of CFL 0.49 each (reading R12)."""
+    n, N, dt = 8, 7, 0.064
+    cfl = dt * (2 * N + 1) * 2 * n / TWO_PI
+    assert 2.4 < cfl < 2.5
+    modes = si.stream_modes(0, 32, 8, 1e-2)
+    ke = {}
+    for nsub in (1, 5):
+        o = Oracle(Grid(2, (n, n), (TWO_PI, TWO_PI)), N, 1e-3, 0.51, dt, rtol_p=1e-10, rtol_v=1e-10,
+                   nsub=nsub)
+        U = []
+        for d in range(2):
+            x, y = o.coords(d)
+            U.append(si.taylor_green_2d(x, y)[d] + si.perturbation_velocity(modes, x, y)[d])
+        x, y = o.coords(None)
+        P = si.taylor_green_2d(x, y)[2]
+        ke[nsub] = [o.kinetic_energy(U)]
+        with np.errstate(all="ignore"):
+            for _ in range(6):
+                U, P, _ = o.step(U, P)
+                ke[nsub].append(o.kinetic_energy(U))
+    assert not (ke[1][-1] < 10 * ke[1][0]), ke[1]          # unstable (or NaN)
+    k5 = np.array(ke[5])
+    assert np.all(np.diff(k5) < 0) and k5[-1] > 0.98 * k5[0], k5
+
+
 def test_projection_accuracy_order():
     """Eq. l2forward on a smooth field: the projection from the dual to the main
     grid converges at order N+1 in the max norm."""
