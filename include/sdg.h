@@ -98,6 +98,19 @@ int sdg_matrices(int N, double* out);
  * Errors: INVALID_ARG. */
 int sdg_kernel_projector(int N, double* proj, int* dim);
 
+/* The 1D line operator the FP64 (fp32 = 0) or FP32 (fp32 != 0) kernels
+ * apply with the accurate contraction, evaluated on the host in extended
+ * precision from the coefficients they store: HL, HR the neighbour blocks
+ * (stand-ins for H^L, H^R after Eq. pSyst) and Mc the centre block H^C
+ * plus the symmetric correction that makes the stored operator vanish on
+ * the local kernel (see sdg_kernel_projector).  Three host arrays of
+ * (N+1)^2 doubles, row-major.  By construction HL = HR^T and Mc = Mc^T
+ * (exactly, up to the extended-precision evaluation) and
+ * (HL + Mc + HR) c = 0 for every kernel pattern c.  The plain FP64 CG
+ * applies HL, H^C-part of Mc without correction, and HR.
+ * Errors: INVALID_ARG. */
+int sdg_line_operator(int N, int fp32, double* HL, double* Mc, double* HR);
+
 /* Create a problem: grid, degree N, viscosity nu >= 0, implicitness
  * theta in [1/2, 1] (Sec. 2.1, P^{n+theta}), time step dt > 0.  Allocates
  * the state (U_d, P) and every work buffer on the current CUDA device.

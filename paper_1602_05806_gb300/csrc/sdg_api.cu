@@ -383,6 +383,17 @@ int sdg_kernel_projector(int N, double* proj, int* dim) {
   return SDG_OK;
 }
 
+int sdg_line_operator(int N, int fp32, double* HL, double* Mc, double* HR) {
+  SDG_ARG(N >= 0 && N <= kMaxN, "N must be in [0, 11]");
+  SDG_ARG(HL && Mc && HR, "NULL output");
+  Basis1D b;
+  build_basis(N, &b);
+  CoefSet c;
+  build_coefs(b, fp32 ? 1 : 0, &c);
+  line_operator(c, HL, Mc, HR);
+  return SDG_OK;
+}
+
 int sdg_create(const sdg_grid* grid, int N, double nu, double theta, double dt, sdg_handle** out) {
   SDG_ARG(grid && out, "NULL argument");
   SDG_ARG(grid->dim == 2 || grid->dim == 3, "dim must be 2 or 3");

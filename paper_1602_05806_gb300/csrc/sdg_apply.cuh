@@ -45,14 +45,17 @@ struct Tile {
   static constexpr int ES = DIM == 2 ? PS : N1 * PS;
 };
 
-// Stored 1D blocks in the compute precision (see CoefSet): H^C symmetric and
-// H^L = (H^R)^T exactly; rho the row sums of [H^L H^C H^R]; for odd N the
-// stored sawtooth pattern z, zn = z / (z.z) and the symmetric correction C.
+// Stored line operator in the compute precision, in the even/odd basis of
+// the line (see CoefSet): H^R = [[A, B], [-B^T, D]], H^L = [[A, -B], [B^T, D]],
+// H^C = diag(CE, CO); kernel correction rho (even N) or the fit and
+// S0 / S1 correction (odd N).
 template <typename T, int N1>
 struct Coef {
-  T HL[N1 * N1], HC[N1 * N1], HR[N1 * N1];
-  T C[(N1 % 2 == 0) ? N1 * N1 : 1];
-  T rho[N1], z[N1], zn[N1];
+  static constexpr int H = N1 / 2, HE = (N1 + 1) / 2, HO = H > 0 ? H : 1;
+  T A[HE * HE], B[HE * HO], D[HO * HO], CE[HE * HE], CO[HO * HO];
+  T rho_e[HE], rho_o[HO];
+  T zn[HO], z2[HO], S0[HO], S1[HO], k1[HO];
+  T k0, inv_n;
 };
 
 template <typename T, int DIM, int N1>
@@ -146,8 +149,16 @@ __device__ __forceinline__ bool slot_elem(int s, const int o[3], int VX, int VY,
 // ACC: accurate contraction (local kernel removal + symmetric correction),
 // used for every FP32 application and for the FP64 true residuals of the
 // mixed solver; plain FP64 CG uses the direct contraction.
+// Blocks per SM the kernel is compiled for (register cap).  2D FP32 with
+// n1 = 8 fits 40 registers without spills, so six 256-thread blocks share
+// an SM (as its shared-memory tile allows); elsewhere the compiler chooses.
+template <typename T, int DIM, int N1>
+constexpr int apply_min_blocks() {
+  return (sizeof(T) == 4 && DIM == 2 && N1 == 8) ? 6 : 1;
+}
+
 template <typename T, int DIM, int N1, bool ACC>
-__global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
+__global__ void __launch_bounds__(Tile<DIM, N1>::THREADS, (apply_min_blocks<T, DIM, N1>()))
     k_apply(const __grid_constant__ ApplyParams<T, DIM, N1> a) {
   using TS = Tile<DIM, N1>;
   constexpr int TX = TS::TX, TY = TS::TY, TZ = TS::TZ, TE = TS::TE;
@@ -266,62 +277,144 @@ __global__ void __launch_bounds__(Tile<DIM, N1>::THREADS)
         xc[k] = s_in[sc * ES + base + k * stride];
         xr[k] = s_in[sr * ES + base + k * stride];
       }
+      // Even/odd form of the three line segments (see Coef): the neighbour
+      // segments enter only through sE = l^_E + r^_E, dE = l^_E - r^_E,
+      // sO = l^_O + r^_O, dO = r^_O - l^_O, the centre through cE, cO.
+      constexpr int H = N1 / 2, HE = (N1 + 1) / 2, HO = H > 0 ? H : 1;
+      constexpr bool MID = (N1 % 2) == 1;
       // Accuracy of the contraction (it matters in FP32).  The operator
-      // annihilates every line-repeated pattern q in its local kernel: the
-      // constants, and for odd N also the sawtooth z.  So q may be removed
-      // from the three line segments before the contractions: with q fitted
-      // to the centre element (c = centre node value, amplitude dz of z from
-      // the centre segment) the operands shrink to the local variation of
-      // smooth fields, and the rounding of the products drops by orders of
-      // magnitude on the smooth and sawtooth-modulated modes whose
-      // eigenvalues are tiny.  The stored blocks do not annihilate q exactly,
-      // so a symmetric correction is applied to the centre operand: -rho_m
-      // (even N) or C (odd N).  The applied operator is then exactly
-      // symmetric and annihilates q, whatever q is.
-      constexpr bool KZ = ACC && (N1 % 2 == 0);  // odd N: two-dimensional local kernel
+      // annihilates every line-repeated pattern q of its local kernel (the
+      // constants; for odd N also the sawtooth z), so q may be removed from
+      // the three segments first: a centre node value c0 (differences of
+      // nearby values are exact), then for odd N the orthogonal fit onto
+      // {1, z} of the centre segment.  The operands shrink to the local
+      // variation of smooth fields, and the rounding of the products drops
+      // by orders of magnitude on the smooth and sawtooth-modulated modes
+      // with tiny eigenvalues.  The stored blocks annihilate q only up to
+      // rounding, so a symmetric correction (-rho, or -k0 S0 - k1 S1) keeps
+      // the applied operator exactly symmetric and exactly zero on q.
+      constexpr bool KZ = ACC && (N1 % 2 == 0);
+      T sE[HE], dE[HE], sO[HO], dO[HO], cE[HE], cO[HO];
       if constexpr (ACC) {
-        const T cref = xc[N1 / 2];
+        const T c0 = xc[N1 / 2];
 #pragma unroll
-        for (int k = 0; k < N1; ++k) {
-          xl[k] -= cref;
-          xc[k] -= cref;
-          xr[k] -= cref;
+        for (int k = 0; k < H; ++k) {
+          const T l0 = xl[k] - c0, l1 = xl[N1 - 1 - k] - c0;
+          const T r0 = xr[k] - c0, r1 = xr[N1 - 1 - k] - c0;
+          sE[k] = (l0 + l1) + (r0 + r1);
+          dE[k] = (l0 - r0) + (l1 - r1);
+          const T lO = l0 - l1, rO = r0 - r1;
+          sO[k] = lO + rO;
+          dO[k] = rO - lO;
+          const T c0k = xc[k] - c0, c1k = xc[N1 - 1 - k] - c0;
+          cE[k] = c0k + c1k;
+          cO[k] = c0k - c1k;
+        }
+        if constexpr (MID) {
+          const T l0 = xl[H] - c0, r0 = xr[H] - c0;
+          sE[H] = l0 + r0;
+          dE[H] = l0 - r0;
+          cE[H] = xc[H] - c0;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+          const T lE = xl[k] + xl[N1 - 1 - k], lO = xl[k] - xl[N1 - 1 - k];
+          const T rE = xr[k] + xr[N1 - 1 - k], rO = xr[k] - xr[N1 - 1 - k];
+          sE[k] = lE + rE;
+          dE[k] = lE - rE;
+          sO[k] = lO + rO;
+          dO[k] = rO - lO;
+          cE[k] = xc[k] + xc[N1 - 1 - k];
+          cO[k] = xc[k] - xc[N1 - 1 - k];
+        }
+        if constexpr (MID) {
+          sE[H] = xl[H] + xr[H];
+          dE[H] = xl[H] - xr[H];
+          cE[H] = xc[H];
         }
       }
       if constexpr (KZ) {
-        T dz = T(0);
+        // orthogonal fit mu 1 + dz z of the centre segment, removed from all three
+        T sum = T(0), dz = T(0);
 #pragma unroll
-        for (int k = 0; k < N1; ++k) dz = fma(a.c.zn[k], xc[k], dz);
+        for (int k = 0; k < H; ++k) {
+          sum += cE[k];
+          dz = fma(a.c.zn[k], cO[k], dz);
+        }
+        const T mu2 = T(2) * (sum * a.c.inv_n);
 #pragma unroll
-        for (int k = 0; k < N1; ++k) {
-          xl[k] = fma(-dz, a.c.z[k], xl[k]);
-          xc[k] = fma(-dz, a.c.z[k], xc[k]);
-          xr[k] = fma(-dz, a.c.z[k], xr[k]);
+        for (int k = 0; k < H; ++k) {
+          cE[k] -= mu2;
+          sE[k] = fma(T(-2), mu2, sE[k]);
+          cO[k] = fma(-dz, a.c.z2[k], cO[k]);
+          sO[k] = fma(T(-2) * dz, a.c.z2[k], sO[k]);
         }
       }
+      // contractions: yE = A sE + B dO + CE cE ; yO = B^T dE + D sO + CO cO
+      T yE[HE], yO[HO];
+#pragma unroll
+      for (int m = 0; m < HE; ++m) {
+        T acc = T(0);
+#pragma unroll
+        for (int j = 0; j < HE; ++j) {
+          acc = fma(a.c.A[m * HE + j], sE[j], acc);
+          acc = fma(a.c.CE[m * HE + j], cE[j], acc);
+        }
+#pragma unroll
+        for (int j = 0; j < H; ++j) acc = fma(a.c.B[m * HO + j], dO[j], acc);
+        yE[m] = acc;
+      }
+#pragma unroll
+      for (int m = 0; m < H; ++m) {
+        T acc = T(0);
+#pragma unroll
+        for (int j = 0; j < HE; ++j) acc = fma(a.c.B[j * HO + m], dE[j], acc);
+#pragma unroll
+        for (int j = 0; j < H; ++j) {
+          acc = fma(a.c.D[m * HO + j], sO[j], acc);
+          acc = fma(a.c.CO[m * HO + j], cO[j], acc);
+        }
+        yO[m] = acc;
+      }
+      if constexpr (KZ) {
+        T al = T(0), be = T(0);
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+          al = fma(a.c.S0[k], cE[k], al);
+          be = fma(a.c.S1[k], cO[k], be);
+        }
+        const T ak = al * a.c.k0;
+#pragma unroll
+        for (int m = 0; m < H; ++m) {
+          yE[m] -= ak;
+          yO[m] = fma(-be, a.c.k1[m], yO[m]);
+        }
+      } else if constexpr (ACC) {
+#pragma unroll
+        for (int m = 0; m < HE; ++m) yE[m] = fma(-a.c.rho_e[m], cE[m], yE[m]);
+#pragma unroll
+        for (int m = 0; m < H; ++m) yO[m] = fma(-a.c.rho_o[m], cO[m], yO[m]);
+      }
+      // back to the nodes: out_k = yE + yO, out_{n-1-k} = yE - yO (scaled)
       const T f = a.s[d] * wp;
+      T val[N1];
+#pragma unroll
+      for (int m = 0; m < H; ++m) {
+        const T t = f * yE[m];
+        val[m] = fma(f, yO[m], t);
+        val[N1 - 1 - m] = fma(-f, yO[m], t);
+      }
+      if constexpr (MID) val[H] = f * yE[H];
       T* out = s_out + te * ES + base;
 #pragma unroll
       for (int m = 0; m < N1; ++m) {
-        T acc = T(0);
-#pragma unroll
-        for (int k = 0; k < N1; ++k) {
-          acc = fma(a.c.HL[m * N1 + k], xl[k], acc);
-          acc = fma(a.c.HC[m * N1 + k], xc[k], acc);
-          acc = fma(a.c.HR[m * N1 + k], xr[k], acc);
-        }
-        if constexpr (KZ) {
-#pragma unroll
-          for (int k = 0; k < N1; ++k) acc = fma(a.c.C[m * N1 + k], xc[k], acc);
-        } else if constexpr (ACC) {
-          acc = fma(-a.c.rho[m], xc[m], acc);
-        }
-        T val = f * acc;
+        T v = val[m];
         if (d == 0) {
-          if (a.cmass != T(0)) val = fma(a.cmass * wp * s_w[m], s_in[sc * ES + base + m * stride], val);
-          out[m * stride] = val;
+          if (a.cmass != T(0)) v = fma(a.cmass * wp * s_w[m], xc[m], v);
+          out[m * stride] = v;
         } else {
-          out[m * stride] += val;
+          out[m * stride] += v;
         }
       }
     }
@@ -388,18 +481,31 @@ cudaError_t launch_apply_acc(const sdg_handle* h, const ApplyArgs<T>& in, cudaSt
   ApplyParams<T, DIM, N1> p;
   const Basis1D& b = h->basis;
   const CoefSet& cs = sizeof(T) == 4 ? h->coef32 : h->coef64;  // values exact in T
-  for (int i = 0; i < N1 * N1; ++i) {
-    p.c.HL[i] = (T)cs.HL[i];
-    p.c.HC[i] = (T)cs.HC[i];
-    p.c.HR[i] = (T)cs.HR[i];
+  constexpr int H = N1 / 2, HE = (N1 + 1) / 2, HO = H > 0 ? H : 1;
+  p.c = Coef<T, N1>{};
+  for (int i = 0; i < HE; ++i)
+    for (int j = 0; j < HE; ++j) {
+      p.c.A[i * HE + j] = (T)cs.A[i * HE + j];
+      p.c.CE[i * HE + j] = (T)cs.CE[i * HE + j];
+    }
+  for (int i = 0; i < HE; ++i)
+    for (int j = 0; j < H; ++j) p.c.B[i * HO + j] = (T)cs.B[i * H + j];
+  for (int i = 0; i < H; ++i)
+    for (int j = 0; j < H; ++j) {
+      p.c.D[i * HO + j] = (T)cs.D[i * H + j];
+      p.c.CO[i * HO + j] = (T)cs.CO[i * H + j];
+    }
+  for (int i = 0; i < HE; ++i) p.c.rho_e[i] = (T)cs.rho_e[i];
+  for (int i = 0; i < H; ++i) {
+    p.c.rho_o[i] = (T)cs.rho_o[i];
+    p.c.zn[i] = (T)cs.zn[i];
+    p.c.z2[i] = (T)cs.z2[i];
+    p.c.S0[i] = (T)cs.S0[i];
+    p.c.S1[i] = (T)cs.S1[i];
+    p.c.k1[i] = (T)cs.k1[i];
   }
-  if constexpr (N1 % 2 == 0)
-    for (int i = 0; i < N1 * N1; ++i) p.c.C[i] = (T)cs.C[i];
-  for (int m = 0; m < N1; ++m) {
-    p.c.rho[m] = (T)cs.rho[m];
-    p.c.z[m] = (T)cs.z[m];
-    p.c.zn[m] = (T)cs.zn[m];
-  }
+  p.c.k0 = (T)cs.k0;
+  p.c.inv_n = (T)cs.inv_n;
   for (int i = 0; i < N1; ++i) p.w[i] = (T)b.w[i];
   p.x = in.x;
   p.p_old = in.p_old;

@@ -282,85 +282,247 @@ int kernel_projector(const Basis1D& b, double* proj) {
   return dim;
 }
 
-void build_coefs(const Basis1D& b, int fp32, CoefSet* c) {
-  const int n = b.n1;
-  auto rnd = [fp32](double v) { return fp32 ? (double)(float)v : v; };
-  for (int i = 0; i < kMaxN1 * kMaxN1; ++i) c->HL[i] = c->HC[i] = c->HR[i] = c->C[i] = 0.0;
-  for (int i = 0; i < kMaxN1; ++i) c->rho[i] = c->z[i] = c->zn[i] = 0.0;
-  for (int m = 0; m < n; ++m)
-    for (int k = 0; k < n; ++k) {
-      c->HR[m * n + k] = rnd(b.HR[m * n + k]);
-      c->HL[m * n + k] = rnd(b.HR[k * n + m]);
-      c->HC[m * n + k] = rnd(0.5 * (b.HC[m * n + k] + b.HC[k * n + m]));
+namespace {
+
+using LD = long double;
+
+// Row-major n x n helpers in long double.
+struct Mat {
+  int n;
+  LD v[kMaxN1 * kMaxN1];
+  LD& at(int i, int j) { return v[i * n + j]; }
+  LD at(int i, int j) const { return v[i * n + j]; }
+};
+
+Mat mat_zero(int n) {
+  Mat m;
+  m.n = n;
+  for (int i = 0; i < n * n; ++i) m.v[i] = 0.0L;
+  return m;
+}
+
+Mat mat_mul(const Mat& a, const Mat& b) {
+  Mat c = mat_zero(a.n);
+  for (int i = 0; i < a.n; ++i)
+    for (int j = 0; j < a.n; ++j) {
+      LD s = 0.0L;
+      for (int k = 0; k < a.n; ++k) s += a.at(i, k) * b.at(k, j);
+      c.at(i, j) = s;
     }
-  std::vector<double> G(n * n);
-  for (int i = 0; i < n * n; ++i) G[i] = c->HL[i] + c->HC[i] + c->HR[i];
-  for (int m = 0; m < n; ++m) {
-    long double rs = 0.0L;
-    for (int k = 0; k < n; ++k) rs += (long double)c->HL[m * n + k] + (long double)c->HC[m * n + k] +
-                                      (long double)c->HR[m * n + k];
-    c->rho[m] = rnd((double)rs);
+  return c;
+}
+
+Mat mat_t(const Mat& a) {
+  Mat c = mat_zero(a.n);
+  for (int i = 0; i < a.n; ++i)
+    for (int j = 0; j < a.n; ++j) c.at(i, j) = a.at(j, i);
+  return c;
+}
+
+// P (even/odd transform, rows: even part, middle, odd part) and Q = G^-1 P.
+void eo_transforms(int n, Mat& P, Mat& Q) {
+  const int h = n / 2, hE = (n + 1) / 2;
+  P = mat_zero(n);
+  Q = mat_zero(n);
+  for (int k = 0; k < h; ++k) {
+    P.at(k, k) = 1.0L;
+    P.at(k, n - 1 - k) = 1.0L;
+    P.at(hE + k, k) = 1.0L;
+    P.at(hE + k, n - 1 - k) = -1.0L;
   }
+  if (n % 2) P.at(h, h) = 1.0L;
+  for (int i = 0; i < n; ++i) {
+    const LD g = (n % 2 && i == h) ? 1.0L : 2.0L;
+    for (int j = 0; j < n; ++j) Q.at(i, j) = P.at(i, j) / g;
+  }
+}
+
+// Stored e/o blocks -> natural-basis H^L, H^C, H^R (long double).
+void effective_blocks(const CoefSet& c, Mat& HL, Mat& HC, Mat& HR) {
+  const int n = c.n, h = c.h, hE = c.hE;
+  Mat P, Q;
+  eo_transforms(n, P, Q);
+  Mat R = mat_zero(n), L = mat_zero(n), C = mat_zero(n);
+  for (int i = 0; i < hE; ++i)
+    for (int j = 0; j < hE; ++j) {
+      R.at(i, j) = L.at(i, j) = c.A[i * hE + j];
+      C.at(i, j) = c.CE[i * hE + j];
+    }
+  for (int i = 0; i < hE; ++i)
+    for (int j = 0; j < h; ++j) {
+      const LD bij = c.B[i * h + j];
+      R.at(i, hE + j) = bij;
+      L.at(i, hE + j) = -bij;
+      R.at(hE + j, i) = -bij;
+      L.at(hE + j, i) = bij;
+    }
+  for (int i = 0; i < h; ++i)
+    for (int j = 0; j < h; ++j) {
+      R.at(hE + i, hE + j) = L.at(hE + i, hE + j) = c.D[i * h + j];
+      C.at(hE + i, hE + j) = c.CO[i * h + j];
+    }
+  const Mat Pt = mat_t(P);
+  HR = mat_mul(Pt, mat_mul(R, P));
+  HL = mat_mul(Pt, mat_mul(L, P));
+  HC = mat_mul(Pt, mat_mul(C, P));
+}
+
+}  // namespace
+
+void build_coefs(const Basis1D& b, int fp32, CoefSet* c) {
+  const int n = b.n1, h = n / 2, hE = (n + 1) / 2;
+  auto rnd = [fp32](LD v) { return fp32 ? (double)(float)v : (double)v; };
+  *c = CoefSet{};
+  c->n = n;
+  c->h = h;
+  c->hE = hE;
+  Mat P, Q;
+  eo_transforms(n, P, Q);
+  Mat HR = mat_zero(n), HC = mat_zero(n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      HR.at(i, j) = b.HR[i * n + j];
+      HC.at(i, j) = 0.5L * ((LD)b.HC[i * n + j] + (LD)b.HC[j * n + i]);
+    }
+  const Mat Qt = mat_t(Q);
+  const Mat R = mat_mul(Q, mat_mul(HR, Qt));  // [[A, B], [-B^T, D]] up to rounding
+  const Mat C = mat_mul(Q, mat_mul(HC, Qt));  // diag(CE, CO) up to rounding
+  for (int i = 0; i < hE; ++i)
+    for (int j = 0; j < hE; ++j) {
+      c->A[i * hE + j] = rnd(0.5L * (R.at(i, j) + R.at(j, i)));
+      c->CE[i * hE + j] = rnd(0.5L * (C.at(i, j) + C.at(j, i)));
+    }
+  for (int i = 0; i < hE; ++i)
+    for (int j = 0; j < h; ++j) c->B[i * h + j] = rnd(0.5L * (R.at(i, hE + j) - R.at(hE + j, i)));
+  for (int i = 0; i < h; ++i)
+    for (int j = 0; j < h; ++j) {
+      c->D[i * h + j] = rnd(0.5L * (R.at(hE + i, hE + j) + R.at(hE + j, hE + i)));
+      c->CO[i * h + j] = rnd(0.5L * (C.at(hE + i, hE + j) + C.at(hE + j, hE + i)));
+    }
+  // line sum of the stored operator in the natural basis
+  Mat EL, EC, ER;
+  effective_blocks(*c, EL, EC, ER);
+  Mat G = mat_zero(n);
+  for (int i = 0; i < n * n; ++i) G.v[i] = EL.v[i] + EC.v[i] + ER.v[i];
   double kb[kMaxN1 * kMaxN1];
   const int kd = kernel_basis(b, kb);
   c->kz = kd >= 2 ? 1 : 0;
-  if (!c->kz) return;
-  // z: the kernel direction orthogonal to the constants, scaled to max 1
+  if (!c->kz) {
+    // rho = G 1, made exactly symmetric under the reversal
+    LD rho[kMaxN1];
+    for (int i = 0; i < n; ++i) {
+      LD s = 0.0L;
+      for (int j = 0; j < n; ++j) s += G.at(i, j);
+      rho[i] = s;
+    }
+    for (int k = 0; k < h; ++k) {
+      const LD r = 0.5L * (rho[k] + rho[n - 1 - k]);
+      c->rho_e[k] = rnd(0.5L * r);
+      c->rho_o[k] = rnd(0.5L * r);
+    }
+    if (n % 2) c->rho_e[h] = rnd(rho[h]);
+    return;
+  }
+  // odd N: z = the kernel direction orthogonal to the constants, made
+  // exactly antisymmetric, max |z| = 1
   double best = -1.0;
-  std::vector<double> z(n);
+  std::vector<LD> z(n, 0.0L);
   for (int j = 0; j < kd; ++j) {
-    double mean = 0.0;
+    LD mean = 0.0L;
     for (int l = 0; l < n; ++l) mean += kb[j * n + l];
     mean /= n;
-    double nrm = 0.0;
+    LD nrm = 0.0L;
     for (int l = 0; l < n; ++l) nrm += (kb[j * n + l] - mean) * (kb[j * n + l] - mean);
-    if (nrm > best) {
-      best = nrm;
+    if ((double)nrm > best) {
+      best = (double)nrm;
       for (int l = 0; l < n; ++l) z[l] = kb[j * n + l] - mean;
     }
   }
-  double zmax = 0.0;
-  for (int l = 0; l < n; ++l) zmax = std::fmax(zmax, std::fabs(z[l]));
-  double zz = 0.0;
-  for (int l = 0; l < n; ++l) {
-    c->z[l] = rnd(z[l] / zmax);
-    zz += c->z[l] * c->z[l];
+  LD zmax = 0.0L;
+  for (int k = 0; k < h; ++k) {
+    const LD a = 0.5L * (z[k] - z[n - 1 - k]);
+    z[k] = a;
+    z[n - 1 - k] = -a;
+    zmax = std::fmax((double)zmax, std::fabs((double)a));
   }
-  for (int l = 0; l < n; ++l) c->zn[l] = rnd(c->z[l] / zz);
-  // orthonormal K = [k0, k1] spanning {1, z_stored} (Gram-Schmidt in FP64)
-  std::vector<double> k0(n, 1.0 / std::sqrt((double)n)), k1(n);
-  double d = 0.0;
-  for (int l = 0; l < n; ++l) d += k0[l] * c->z[l];
-  double nn = 0.0;
-  for (int l = 0; l < n; ++l) { k1[l] = c->z[l] - d * k0[l]; nn += k1[l] * k1[l]; }
-  nn = std::sqrt(nn);
-  for (int l = 0; l < n; ++l) k1[l] /= nn;
-  // S = G K; C = -(S K^T + K S^T - K (K^T S) K^T)
-  std::vector<double> S0(n), S1(n);
-  for (int m = 0; m < n; ++m) {
-    double a = 0.0, bb = 0.0;
-    for (int k = 0; k < n; ++k) { a += G[m * n + k] * k0[k]; bb += G[m * n + k] * k1[k]; }
-    S0[m] = a;
-    S1[m] = bb;
+  LD zz = 0.0L;
+  for (int k = 0; k < h; ++k) {
+    const double zk = rnd(z[k] / zmax);
+    z[k] = zk;
+    z[n - 1 - k] = -zk;
+    zz += 2.0L * (LD)zk * (LD)zk;
   }
-  double KS[2][2] = {{0, 0}, {0, 0}};
-  for (int l = 0; l < n; ++l) {
-    KS[0][0] += k0[l] * S0[l]; KS[0][1] += k0[l] * S1[l];
-    KS[1][0] += k1[l] * S0[l]; KS[1][1] += k1[l] * S1[l];
+  for (int k = 0; k < h; ++k) {
+    c->z2[k] = 2.0 * (double)z[k];  // exact
+    c->zn[k] = rnd(z[k] / zz);
   }
-  for (int p = 0; p < n; ++p)
-    for (int q = 0; q < n; ++q) {
-      const double skt = S0[p] * k0[q] + S1[p] * k1[q];
-      const double kst = k0[p] * S0[q] + k1[p] * S1[q];
-      const double kk = k0[p] * (KS[0][0] * k0[q] + KS[0][1] * k1[q]) + k1[p] * (KS[1][0] * k0[q] + KS[1][1] * k1[q]);
-      c->C[p * n + q] = -(skt + kst - kk);
+  // orthonormal kernel basis k0 = 1/sqrt(n), k1 = z/|z|; S = G [k0, k1]
+  const LD k0 = 1.0L / std::sqrt((LD)n), znorm = std::sqrt(zz);
+  LD S0[kMaxN1], S1[kMaxN1];
+  for (int i = 0; i < n; ++i) {
+    LD a = 0.0L, bb = 0.0L;
+    for (int j = 0; j < n; ++j) {
+      a += G.at(i, j) * k0;
+      bb += G.at(i, j) * (z[j] / znorm);
     }
-  for (int p = 0; p < n; ++p)
-    for (int q = p + 1; q < n; ++q) {
-      const double v = rnd(0.5 * (c->C[p * n + q] + c->C[q * n + p]));
-      c->C[p * n + q] = c->C[q * n + p] = v;
+    S0[i] = a;
+    S1[i] = bb;
+  }
+  for (int k = 0; k < h; ++k) {
+    c->S0[k] = rnd(0.5L * (S0[k] + S0[n - 1 - k]));
+    c->S1[k] = rnd(0.5L * (S1[k] - S1[n - 1 - k]));
+    c->k1[k] = rnd(z[k] / znorm);
+  }
+  c->k0 = rnd(k0);
+  c->inv_n = rnd(1.0L / n);
+}
+
+void line_operator(const CoefSet& c, double* HLo, double* Mco, double* HRo) {
+  const int n = c.n, h = c.h, hE = c.hE;
+  Mat EL, EC, ER;
+  effective_blocks(c, EL, EC, ER);
+  Mat P, Q;
+  eo_transforms(n, P, Q);
+  for (int j = 0; j < n; ++j) {
+    // centre line e_j: fit, shifted line, correction (as the kernel does)
+    LD x[kMaxN1], q[kMaxN1];
+    for (int i = 0; i < n; ++i) { x[i] = (i == j) ? 1.0L : 0.0L; q[i] = 0.0L; }
+    LD xE[kMaxHalf], xO[kMaxHalf];
+    for (int k = 0; k < h; ++k) { xE[k] = x[k] + x[n - 1 - k]; xO[k] = x[k] - x[n - 1 - k]; }
+    if (n % 2) xE[h] = x[h];
+    LD yE[kMaxHalf] = {0}, yO[kMaxHalf] = {0};
+    if (c.kz) {
+      LD sum = 0.0L, dz = 0.0L;
+      for (int k = 0; k < h; ++k) { sum += xE[k]; dz += (LD)c.zn[k] * xO[k]; }
+      const LD mu = sum * (LD)c.inv_n;
+      for (int k = 0; k < h; ++k) {
+        q[k] = mu + dz * 0.5L * (LD)c.z2[k];
+        q[n - 1 - k] = mu - dz * 0.5L * (LD)c.z2[k];
+        xE[k] -= 2.0L * mu;
+        xO[k] -= dz * (LD)c.z2[k];
+      }
+      LD al = 0.0L, be = 0.0L;
+      for (int k = 0; k < h; ++k) { al += (LD)c.S0[k] * xE[k]; be += (LD)c.S1[k] * xO[k]; }
+      for (int k = 0; k < h; ++k) { yE[k] = -al * (LD)c.k0; yO[k] = -be * (LD)c.k1[k]; }
+    } else {
+      for (int k = 0; k < hE; ++k) yE[k] = -(LD)c.rho_e[k] * xE[k];
+      for (int k = 0; k < h; ++k) yO[k] = -(LD)c.rho_o[k] * xO[k];
     }
-  for (int p = 0; p < n; ++p) c->C[p * n + p] = rnd(c->C[p * n + p]);
+    for (int i = 0; i < n; ++i) {
+      LD s = 0.0L;
+      for (int k = 0; k < n; ++k) s += EC.at(i, k) * (x[k] - q[k]) - (EL.at(i, k) + ER.at(i, k)) * q[k];
+      // correction back to the natural basis
+      LD corr;
+      if (i < h) corr = yE[i] + yO[i];
+      else if (n % 2 && i == h) corr = yE[h];
+      else corr = yE[n - 1 - i] - yO[n - 1 - i];
+      Mco[i * n + j] = (double)(s + corr);
+    }
+  }
+  for (int i = 0; i < n * n; ++i) {
+    HLo[i] = (double)EL.v[i];
+    HRo[i] = (double)ER.v[i];
+  }
 }
 
 }  // namespace sdg

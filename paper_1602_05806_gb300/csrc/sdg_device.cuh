@@ -84,8 +84,11 @@ __device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
 }
 
 // Sum K float pairs over the block; totals (as doubles) in every thread.
+// Warps and then warp 0 add pairs with TwoSum; only the block total is
+// converted to FP64 (one thread).  s_red: at least 32*K doubles.
 template <int K>
 __device__ __forceinline__ void block_sum_f2(F2 (&v)[K], double* s_red, double (&out)[K]) {
+  float2* s2 = reinterpret_cast<float2*>(s_red);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nw = (blockDim.x + 31) >> 5;
 #pragma unroll
@@ -96,15 +99,24 @@ __device__ __forceinline__ void block_sum_f2(F2 (&v)[K], double* s_red, double (
       F2 u{__shfl_xor_sync(0xffffffffu, t.hi, o), __shfl_xor_sync(0xffffffffu, t.lo, o)};
       t = f2_add(t, u);
     }
-    if (lane == 0) s_red[k * 32 + wid] = (double)t.hi + (double)t.lo;
+    if (lane == 0) s2[k * 32 + wid] = make_float2(t.hi, t.lo);
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (wid == 0) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      double a = 0.0;
-      for (int w = 0; w < nw; ++w) a += s_red[k * 32 + w];
-      s_red[k * 32] = a;
+      F2 t{0.0f, 0.0f};
+      if (lane < nw) {
+        const float2 q = s2[k * 32 + lane];
+        t = F2{q.x, q.y};
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        F2 u{__shfl_xor_sync(0xffffffffu, t.hi, o), __shfl_xor_sync(0xffffffffu, t.lo, o)};
+        t = f2_add(t, u);
+      }
+      // every lane of warp 0 has read its slot before the shuffles above
+      if (lane == 0) s_red[k * 32] = (double)t.hi + (double)t.lo;
     }
   }
   __syncthreads();

@@ -128,24 +128,41 @@ __global__ void __launch_bounds__(kThreads)
   const long long nv = n / W;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
-  for (long long i = tid; i < nv; i += nth) {
-    V xv = reinterpret_cast<V*>(x)[i], rv = reinterpret_cast<V*>(r)[i];
-    const V pv = reinterpret_cast<const V*>(p)[i], av = reinterpret_cast<const V*>(Ap)[i];
-    T* xs = reinterpret_cast<T*>(&xv);
-    T* rs = reinterpret_cast<T*>(&rv);
-    const T* ps = reinterpret_cast<const T*>(&pv);
-    const T* as = reinterpret_cast<const T*>(&av);
+  // U vectors per thread and pass, all loads issued before the arithmetic
+  // (the update is bound by memory latency, not bandwidth, at one vector)
+  constexpr int U = 2;
+  for (long long i0 = tid; i0 < nv; i0 += U * nth) {
+    V xv[U], rv[U], pv[U], av[U];
 #pragma unroll
-    for (int k = 0; k < W; ++k) upd1(xs[k], rs[k], ps[k], as[k], alpha, rr);
-    reinterpret_cast<V*>(x)[i] = xv;
-    reinterpret_cast<V*>(r)[i] = rv;
-    if (defl) {
-      const unsigned l0 = (unsigned)((unsigned long long)(i * W) % (unsigned)df.npe);
+    for (int u = 0; u < U; ++u) {
+      const long long i = i0 + u * nth;
+      if (i < nv) {
+        xv[u] = reinterpret_cast<V*>(x)[i];
+        rv[u] = reinterpret_cast<V*>(r)[i];
+        pv[u] = reinterpret_cast<const V*>(p)[i];
+        av[u] = reinterpret_cast<const V*>(Ap)[i];
+      }
+    }
 #pragma unroll
-      for (int k = 0; k < W; ++k) {
-        unsigned l = l0 + k;
-        if (l >= (unsigned)df.npe) l -= df.npe;
-        atomicAdd(&s_k[l], (float)rs[k]);
+    for (int u = 0; u < U; ++u) {
+      const long long i = i0 + u * nth;
+      if (i >= nv) break;
+      T* xs = reinterpret_cast<T*>(&xv[u]);
+      T* rs = reinterpret_cast<T*>(&rv[u]);
+      const T* ps = reinterpret_cast<const T*>(&pv[u]);
+      const T* as = reinterpret_cast<const T*>(&av[u]);
+#pragma unroll
+      for (int k = 0; k < W; ++k) upd1(xs[k], rs[k], ps[k], as[k], alpha, rr);
+      reinterpret_cast<V*>(x)[i] = xv[u];
+      reinterpret_cast<V*>(r)[i] = rv[u];
+      if (defl) {
+        const unsigned l0 = (unsigned)((unsigned long long)(i * W) % (unsigned)df.npe);
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          unsigned l = l0 + k;
+          if (l >= (unsigned)df.npe) l -= df.npe;
+          atomicAdd(&s_k[l], (float)rs[k]);
+        }
       }
     }
   }

@@ -27,7 +27,7 @@ SDG_MIXED = 1
 
 # every symbol include/sdg.h declares
 EXPORTS = (
-    "sdg_nodes", "sdg_matrices", "sdg_kernel_projector", "sdg_create", "sdg_destroy", "sdg_set_options",
+    "sdg_nodes", "sdg_matrices", "sdg_kernel_projector", "sdg_line_operator", "sdg_create", "sdg_destroy", "sdg_set_options",
     "sdg_set_mixed_options", "sdg_set_convection_substeps", "sdg_ndof", "sdg_set_state", "sdg_get_state",
     "sdg_pressure_apply", "sdg_viscous_apply", "sdg_pressure_cg", "sdg_viscous_cg",
     "sdg_dual_to_main", "sdg_main_to_dual", "sdg_convect", "sdg_pressure_rhs",
@@ -75,6 +75,7 @@ def lib():
         L.sdg_nodes.argtypes = [ip, dp, dp]
         L.sdg_matrices.argtypes = [ip, dp]
         L.sdg_kernel_projector.argtypes = [ip, dp, ctypes.POINTER(ctypes.c_int)]
+        L.sdg_line_operator.argtypes = [ip, ip, dp, dp, dp]
         L.sdg_create.argtypes = [ctypes.POINTER(sdg_grid), ip, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_double, ctypes.POINTER(vp)]
         L.sdg_destroy.argtypes = [vp]
@@ -156,6 +157,16 @@ def sdg_matrices(N):
     check(lib().sdg_matrices(N, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     names = ("M", "Rt", "Lt", "Rb", "Lb", "ML", "MR", "HR", "HL", "HC")
     return {k: out[i * m:(i + 1) * m].reshape(N + 1, N + 1).copy() for i, k in enumerate(names)}
+
+
+def sdg_line_operator(N, fp32=False):
+    """(HL, Mc, HR): the stored 1D line operator of the accurate contraction
+    in FP64 or FP32, evaluated on the host (see include/sdg.h)."""
+    n1 = N + 1
+    out = [np.zeros((n1, n1)) for _ in range(3)]
+    ptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    check(lib().sdg_line_operator(N, 1 if fp32 else 0, ptr(out[0]), ptr(out[1]), ptr(out[2])))
+    return tuple(out)
 
 
 def sdg_kernel_projector(N):

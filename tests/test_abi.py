@@ -80,3 +80,38 @@ def test_kernel_projector_matches_oracle_kernel(libpath):
         Ax = o.pressure_apply(x)
         scale = np.abs(o.dense(o.pressure_apply)).max() if N <= 4 else 1e3
         assert np.abs(Ax).max() <= 1e-11 * scale * max(1.0, np.abs(x).max())
+
+
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_stored_line_operator(libpath, fp32):
+    """The line operator the kernels store (even/odd blocks, rounded to the
+    compute precision, plus the kernel correction), evaluated on the host:
+    exactly symmetric as a global operator (H^L = (H^R)^T, centre block
+    symmetric), with a null space of the dimension of the local kernel that
+    is the oracle's kernel up to the rounding of the stored sawtooth, and
+    within the rounding of the compute precision of the oracle's blocks."""
+    import numpy as np
+    from oracle import Basis
+    from paper_1602_05806_gb300 import sdg
+    eps = 2.0**-24 if fp32 else 2.0**-53
+    for N in range(12):
+        HL, Mc, HR = sdg.sdg_line_operator(N, bool(fp32))
+        B = Basis(N)
+        s = max(np.abs(B.HR).max(), np.abs(B.HC).max())
+        assert np.abs(HL - HR.T).max() <= 1e-15 * s, N
+        assert np.abs(Mc - Mc.T).max() <= 1e-14 * s, N
+        # local kernel of R~ - L~ (oracle matrices, numpy SVD)
+        _, sv, vt = np.linalg.svd(B.Rt - B.Lt)
+        K = vt[sv <= 1e-10 * max(1.0, sv.max())]
+        kd = K.shape[0]
+        assert kd == (1 if N % 2 == 0 else 2)
+        G = HL + Mc + HR
+        assert np.abs(G.sum(axis=1)).max() <= 1e-14 * s, N   # constants exactly
+        _, gs, gvt = np.linalg.svd(G)
+        assert np.all(gs[-kd:] <= 1e-14 * s), (N, gs)
+        V0 = gvt[-kd:]
+        off = K.T - V0.T @ (V0 @ K.T)
+        assert np.abs(off).max() <= (1e-6 if fp32 else 1e-12), N
+        tol = 8 * eps * (N + 1) * s
+        assert np.abs(HL - B.HL).max() <= tol and np.abs(HR - B.HR).max() <= tol, N
+        assert np.abs(Mc - B.HC).max() <= tol, N
