@@ -235,6 +235,35 @@ int sdg_velocity_update(sdg_handle* h, const double* const* Ustar,
  * info may be NULL.  Returns the first non-OK solve status, or OK. */
 int sdg_step(sdg_handle* h, int nsteps, sdg_step_info* info, void* stream);
 
+/* ---------------------------------------------------------------- batches */
+
+/* A batch of independent problems of uneven size and degree (each one the
+ * scheme of Sec. 2 on its own grid), stepped together.  Every member is an
+ * sdg_handle with its own non-blocking CUDA stream; sdg_batch_step advances
+ * the members concurrently from a pool of host threads (largest first), so
+ * that many small problems occupy the GPU at once. */
+typedef struct sdg_batch sdg_batch;
+
+/* nprob members: grids[i], degree N[i], viscosity nu[i] (host arrays), all
+ * with the same theta and dt.  Argument rules and errors as sdg_create, per
+ * member; on error no batch is returned. */
+int sdg_batch_create(const sdg_grid* grids, const int* N, const double* nu,
+                     int nprob, double theta, double dt, sdg_batch** out);
+int sdg_batch_destroy(sdg_batch* b);
+/* Number of members (0 for NULL). */
+int sdg_batch_size(const sdg_batch* b);
+/* Member i (owned by the batch: do not destroy it), for sdg_set_state,
+ * sdg_get_state, sdg_set_options, sdg_set_convection_substeps and the other
+ * per-handle calls.  Errors: INVALID_ARG. */
+int sdg_batch_member(sdg_batch* b, int i, sdg_handle** h);
+/* Host threads used by sdg_batch_step (default min(nprob, 16, cores)). */
+int sdg_batch_set_threads(sdg_batch* b, int nthreads);
+/* nsteps steps of every member (as sdg_step), ordered after the work queued
+ * on `stream` before the call and before the work queued on it after.
+ * info: host array of nprob entries, or NULL.  Returns the first non-OK
+ * member status (by index); sdg_last_error names the member. */
+int sdg_batch_step(sdg_batch* b, int nsteps, sdg_step_info* info, void* stream);
+
 /* ---------------------------------------------------------------- instrumentation */
 
 /* enable != 0: bracket every launch of the fused CG operator kernel with CUDA

@@ -15,6 +15,7 @@
 // box with vector stores and (CG mode) reduces p^T A p.
 #pragma once
 
+#include <atomic>
 #include <type_traits>
 
 #include "sdg_device.cuh"
@@ -526,12 +527,15 @@ cudaError_t launch_apply_acc(const sdg_handle* h, const ApplyArgs<T>& in, cudaSt
   const long long nblk = (long long)p.ntile[0] * p.ntile[1] * p.ntile[2];
   if (nblk > h->max_blocks) return cudaErrorInvalidConfiguration;
   const size_t smem = (size_t)(TS::NSLOT + TS::TE) * TS::ES * sizeof(T);
-  static bool attr_set = false;  // per instantiation; smem need is fixed
-  if (!attr_set) {
+  // per instantiation (its shared-memory need is fixed); handles of a batch
+  // launch from several host threads, and setting the attribute twice is
+  // harmless
+  static std::atomic<bool> attr_set{false};
+  if (!attr_set.load(std::memory_order_acquire)) {
     cudaError_t e = cudaFuncSetAttribute(k_apply<T, DIM, N1, ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_set.store(true, std::memory_order_release);
   }
   k_apply<T, DIM, N1, ACC><<<(unsigned)nblk, TS::THREADS, smem, stream>>>(p);
   return cudaGetLastError();

@@ -32,7 +32,8 @@ EXPORTS = (
     "sdg_pressure_apply", "sdg_viscous_apply", "sdg_pressure_cg", "sdg_viscous_cg",
     "sdg_dual_to_main", "sdg_main_to_dual", "sdg_convect", "sdg_pressure_rhs",
     "sdg_velocity_update", "sdg_step", "sdg_set_profiling", "sdg_counters", "sdg_diagnostics",
-    "sdg_kinetic_energy_noalloc", "sdg_strerror", "sdg_last_error",
+    "sdg_kinetic_energy_noalloc", "sdg_batch_create", "sdg_batch_destroy", "sdg_batch_size",
+    "sdg_batch_member", "sdg_batch_set_threads", "sdg_batch_step", "sdg_strerror", "sdg_last_error",
 )
 
 
@@ -104,6 +105,13 @@ def lib():
         L.sdg_strerror.argtypes = [ip]
         L.sdg_strerror.restype = ctypes.c_char_p
         L.sdg_last_error.restype = ctypes.c_char_p
+        L.sdg_batch_create.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp, ip, ctypes.c_double,
+                                       ctypes.c_double, ctypes.POINTER(ctypes.c_void_p)]
+        L.sdg_batch_destroy.argtypes = [vp]
+        L.sdg_batch_size.argtypes = [vp]
+        L.sdg_batch_member.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_void_p)]
+        L.sdg_batch_set_threads.argtypes = [vp, ip]
+        L.sdg_batch_step.argtypes = [vp, ip, vp, vp]
         for f in EXPORTS:
             if f not in ("sdg_ndof", "sdg_strerror", "sdg_last_error"):
                 getattr(L, f).restype = ctypes.c_int
@@ -206,9 +214,12 @@ class Handle:
         self.nu, self.theta, self.dt = nu, theta, dt
         self.ndof = int(lib().sdg_ndof(h))
 
+    _owned = True
+
     def close(self):
         if getattr(self, "h", None):
-            lib().sdg_destroy(self.h)
+            if self._owned:
+                lib().sdg_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -298,3 +309,67 @@ class Handle:
         dv = ctypes.c_double()
         check(lib().sdg_diagnostics(self.h, ctypes.byref(ke), ctypes.byref(dv), _stream(stream)))
         return ke.value, dv.value
+
+
+def _step_info_dict(info, dim, rc):
+    return {"status": rc, "pressure": info.pressure.as_dict(),
+            "viscous": [info.viscous[c].as_dict() for c in range(dim)],
+            "pressure_ms": info.pressure_ms, "step_ms": info.step_ms,
+            "pressure_applies": info.pressure_applies, "kernel_launches": info.kernel_launches}
+
+
+class Batch:
+    """Owns an sdg_batch of independent 2D/3D problems.  members[i] is a
+    non-owning Handle view of member i."""
+
+    def __init__(self, problems, theta, dt):
+        """problems: list of (dim, n, L, N, nu)."""
+        k = len(problems)
+        grids = (sdg_grid * k)()
+        Ns = (ctypes.c_int * k)()
+        nus = (ctypes.c_double * k)()
+        for i, (dim, n, L, N, nu) in enumerate(problems):
+            grids[i].dim = dim
+            for d in range(3):
+                grids[i].n[d] = int(n[d]) if d < dim else 1
+                grids[i].L[d] = float(L[d]) if d < dim else 1.0
+            Ns[i] = int(N)
+            nus[i] = float(nu)
+        b = ctypes.c_void_p()
+        check(lib().sdg_batch_create(grids, Ns, nus, k, float(theta), float(dt), ctypes.byref(b)))
+        self.b = b
+        self.members = []
+        for i, (dim, n, L, N, nu) in enumerate(problems):
+            h = ctypes.c_void_p()
+            check(lib().sdg_batch_member(b, i, ctypes.byref(h)))
+            m = Handle.__new__(Handle)
+            m.h, m._owned = h, False
+            m.dim, m.n, m.L, m.N = dim, tuple(n[:dim]), tuple(L[:dim]), N
+            m.nu, m.theta, m.dt = nu, theta, dt
+            m.ndof = int(lib().sdg_ndof(h))
+            self.members.append(m)
+
+    def __len__(self):
+        return len(self.members)
+
+    def set_threads(self, n):
+        check(lib().sdg_batch_set_threads(self.b, int(n)))
+
+    def step(self, nsteps=1, stream=None, ok=(SDG_OK,)):
+        k = len(self.members)
+        info = (sdg_step_info * k)()
+        rc = check(lib().sdg_batch_step(self.b, int(nsteps), info, _stream(stream)), ok)
+        return rc, [_step_info_dict(info[i], self.members[i].dim, rc) for i in range(k)]
+
+    def close(self):
+        if getattr(self, "b", None):
+            for m in self.members:
+                m.h = None
+            lib().sdg_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

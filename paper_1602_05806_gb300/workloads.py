@@ -109,3 +109,33 @@ def workload_state(name, n_override=None):
     w["cfl"] = cfl_number(dim, w["n"], L, w["N"], w["dt"], umax)
     w["nsub"] = convection_substeps(w["cfl"]) if w["cfl"] >= 1.0 else 1
     return w, U, P
+
+
+# Batched workload: 48 independent 2D problems (seed 2): cells per side from
+# {16, 32, 64, 128}, N in 2..11, nu log-uniform in [1e-4, 1e-1]; each one
+# Taylor-Green plus an 8-mode perturbation (amplitude 1e-2, member i seeded
+# with 1000 * seed + i), theta = 0.51, dt = 1e-3, 50 steps.
+BATCH = dict(seed=2, count=48, theta=0.51, dt=1e-3, steps=50, nmodes=8, kmax=8, amplitude=1e-2)
+
+
+def batch_workload(seed=None, count=None):
+    """(params, problems, states): problems[i] = (2, (c, c), L, N, nu) and
+    states[i] = (U list, P) of member i, with params["nsub"][i] its
+    convection sub-steps (1 unless dt exceeds the limit of Eq. CFL1)."""
+    w = dict(BATCH)
+    if seed is not None:
+        w["seed"] = seed
+    if count is not None:
+        w["count"] = count
+    L = (TWO_PI, TWO_PI)
+    problems, states, nsub = [], [], []
+    for i, m in enumerate(si.batch_members(w["seed"], w["count"])):
+        n = (m.cells, m.cells)
+        modes = si.stream_modes(1000 * w["seed"] + i, w["nmodes"], w["kmax"], w["amplitude"])
+        U, P = taylor_green_state(2, n, L, m.N, modes=modes)
+        cfl = cfl_number(2, n, L, m.N, w["dt"], [float(np.abs(u).max()) for u in U])
+        problems.append((2, n, L, m.N, m.nu))
+        states.append((U, P))
+        nsub.append(convection_substeps(cfl) if cfl >= 1.0 else 1)
+    w["nsub"] = nsub
+    return w, problems, states
