@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed plain-FP64 steps (after one warm-up)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=1,
+                    help="timed steps of the 48-problem batch (after one warm-up); 0 skips it")
     return ap.parse_args()
 
 
@@ -126,6 +128,19 @@ def ncu_traffic():
     with open(p) as f:
         d = json.load(f)
     return d.get(WORKLOAD, {}).get("fused_apply_f32_bytes")
+
+
+def reduce_over_ranks(dist, step_ms, solve_ms, work, device):
+    """Whole-job numbers of independent replicas: the slowest rank's times
+    (max) and the work of all ranks (sum).  dist None: a single process."""
+    if dist is None:
+        return step_ms, solve_ms, work
+    import torch
+    t = torch.tensor([step_ms, solve_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor([work], dtype=torch.float64, device=device)
+    dist.all_reduce(w)
+    return float(t[0]), float(t[1]), float(w[0])
 
 
 # ----------------------------------------------------------------- oracle timing
@@ -229,8 +244,7 @@ def run_ours(args):
         info = h.step(1)
         assert info["status"] == sdg.SDG_OK, info
 
-    # ---- timed mixed steps
-    h.set_profiling(True)
+    # ---- timed mixed steps (no per-launch instrumentation inside)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     sampler = ClockSampler(local)
     torch.cuda.synchronize()
@@ -254,21 +268,19 @@ def run_ours(args):
     barrier()
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
+
+    # ---- one more step with CUDA events around every launch of the fused
+    # FP32 operator (on the launch stream), for its roofline
+    h.set_profiling(True)
+    flush.fill_(-1.0)
+    info = h.step(1)
+    assert info["status"] == sdg.SDG_OK, info
     cnt = h.counters()
     h.set_profiling(False)
 
     tot_step_ms = sum(step_ms)
     # max over ranks of the times, sum of the work
-    if dist is not None:
-        t = torch.tensor([tot_step_ms, p_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_step_ms, p_ms_max = float(t[0]), float(t[1])
-        wk = torch.tensor([float(ndof * p_applies)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(wk)
-        work = float(wk[0])
-    else:
-        p_ms_max = p_ms
-        work = float(ndof * p_applies)
+    tot_step_ms, p_ms_max, work = reduce_over_ranks(dist, tot_step_ms, p_ms, float(ndof * p_applies), "cuda")
     value = work / (p_ms_max * 1e-3) / 1e9
 
     # ---- dominant kernel: fused FP32 CG operator (roofline)
@@ -291,7 +303,8 @@ def run_ours(args):
     else:
         roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
                     "frac": frac_alu, "traffic": traffic}
-    roofline.update({"kernel": "k_apply<float,2,8> (fused CG: p = r + beta p, A p, p.Ap)",
+    roofline.update({"kernel": "k_apply<float,2,8> (fused CG: p = r + beta p, A p, p.Ap; timed in one "
+                               "extra step with events around each launch)",
                      "avg_launch_us": avg_ms * 1e3, "launches_timed": n32,
                      "peak_source": peak_src + (" (hbm_gbs)" if roofline["bound"] == "hbm"
                                                 else " (152 SM x 128 FP32 lanes x 2 x sm_max_mhz)"),
@@ -363,6 +376,37 @@ def run_ours(args):
                "h2d_bytes_per_step": 3 * ndof * 8, "d2h_bytes_per_step": 3 * ndof * 8,
                "ms_per_step": 1000 * t_tot / args.e2e_steps}
 
+    # ---- batched workload: 48 independent problems stepped concurrently
+    batch = None
+    if args.batch_steps > 0:
+        from paper_1602_05806_gb300.workloads import batch_workload
+        bw, problems, states = batch_workload()
+        bt = sdg.Batch(problems, bw["theta"], bw["dt"])
+        for i, (U, P) in enumerate(states):
+            m = bt.members[i]
+            m.set_options(sdg.SDG_MIXED, 1e-12, 1e-12)
+            m.set_convection_substeps(bw["nsub"][i])
+            m.set_state([dev(u) for u in U], dev(P))
+        rc, _ = bt.step(1)  # warm-up
+        assert rc == sdg.SDG_OK
+        flush.fill_(0.5)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        rc, infos = bt.step(args.batch_steps, stream=stream)
+        e.record(stream)
+        torch.cuda.synchronize()
+        assert rc == sdg.SDG_OK
+        ms = a.elapsed_time(e)
+        work = sum(m.ndof * inf["pressure_applies"] for m, inf in zip(bt.members, infos))
+        batch = {"workload": "batch48_seed2 (2D, 16^2..128^2 cells, N 2..11, mixed, rtol 1e-12)",
+                 "problems": len(bt), "dof_total": sum(m.ndof for m in bt.members),
+                 "steps": args.batch_steps, "warmup": 1, "ms_per_step": ms / args.batch_steps,
+                 "pressure_gdof_applies_per_s": work / (ms * 1e-3) / 1e9,
+                 "pressure_iters_max": max(inf["pressure"]["iters"] for inf in infos),
+                 "threads": "min(48, 16, cores) host threads, one stream per member"}
+        bt.close()
+
     # ---- CPU baseline (rank 0, N = 1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -384,7 +428,7 @@ def run_ours(args):
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "pressure_iters_per_step": p_iters, "pressure_ms_total": p_ms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "fp64": fp64, "accuracy": accuracy}
+                "clocks": clocks, "fp64": fp64, "accuracy": accuracy, "batch": batch}
         print(json.dumps(line), flush=True)
     h.close()
     if dist is not None:
