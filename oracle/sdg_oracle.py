@@ -514,7 +514,7 @@ class Oracle:
             vec.append(V)
         return np.array(lam), np.array(vec)  # (n, n1), (n, n1, n1)
 
-    def block_circulant_solve(self, b, x0, cmass, scale):
+    def block_circulant_solve(self, b, x0, cmass, scale, raw=False):
         """Exact solution of (cmass M^{xyz} + scale * A') x = b on the periodic
         grid, A' = dt sum_d (1/dx_d^2) M^{perp d} H_d (Eq. pSyst).  The operator
         is block-circulant: a discrete Fourier transform over the elements of
@@ -523,7 +523,9 @@ class Oracle:
         direction d)] W^{1/2} with S_d = W^{-1/2} (H^L e^{-ik} + H^C +
         H^R e^{ik}) W^{-1/2}, which the 1D eigenvectors of the S_d
         diagonalise.  Zero eigenvalues (the kernel, cmass = 0) are dropped and
-        the kernel part of x0 is kept, as CG from x0 does."""
+        the kernel part of x0 is kept, as CG from x0 does (raw: the spectral
+        solution itself, W-orthogonal to the kernel, is returned; this map is
+        symmetric, the projected one is not)."""
         dim = self.dim
         eax = [self._eax(d) for d in range(dim)]
         lax = [self._lax(d) for d in range(dim)]
@@ -564,7 +566,7 @@ class Oracle:
             shp[lax[d]] = self.n1
             Y = Y / sq.reshape(shp)
         x = np.real(np.fft.ifftn(Y, axes=eax))
-        if cmass == 0.0:
+        if cmass == 0.0 and not raw:
             x = x - self.kernel_part(x) + self.kernel_part(x0)
         return x
 
