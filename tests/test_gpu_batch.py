@@ -107,7 +107,9 @@ def test_batch_members_match_single_handles_and_oracle():
         tol = 1e-11 if prec == sdg.SDG_FP64 else 1e-10
         for d in range(dim):
             assert rel(host(Ub[d]), U[d]) <= tol, (i, d)
-        assert rel(host(Pb), P) <= 1e-10, i
+        # the mixed solve may stop at its FP64 true-residual floor (up to
+        # 10 rtol), which the smoothest pressure modes amplify
+        assert rel(host(Pb), P) <= (1e-10 if prec == sdg.SDG_FP64 else 1e-9), i
         singles[i].close()
     b.close()
 
