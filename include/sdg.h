@@ -235,6 +235,29 @@ int sdg_velocity_update(sdg_handle* h, const double* const* Ustar,
  * info may be NULL.  Returns the first non-OK solve status, or OK. */
 int sdg_step(sdg_handle* h, int nsteps, sdg_step_info* info, void* stream);
 
+/* ---------------------------------------------------------------- adjoint */
+
+/* Adjoint (reverse-mode derivative) of one sdg_step, with respect to the
+ * state and the viscosity, for gradient-based use of the scheme.  The step
+ * is differentiated stage by stage as a map (U^n, P^n, nu) -> (U^{n+1},
+ * P^{n+1}) with both linear systems solved exactly: transposed projections
+ * (Eqs. l2forward, l2backward), the transposed velocity update and pressure
+ * right-hand side (Eqs. LOvelocityU-W, pSDG1, pSyst), the pressure and
+ * viscous solves (symmetric operators: one CG each with the same kernels),
+ * the gauge and the kernel part of P (reading R3), and the Rusanov
+ * convection (Eqs. Fu-Fw) linearised at the recomputed RK3 stages, with the
+ * sub-gradient of the larger side of the flux speed 2 max(|v-|, |v+|).
+ *   U:    dim device arrays, the dual-grid velocities at the start of the
+ *         step (the checkpoint; the stages are recomputed from it).
+ *   lamU: dim device arrays; in: d loss / d U^{n+1}; out: d loss / d U^n.
+ *   lamP: device array; in: d loss / d P^{n+1}; out: d loss / d P^n.
+ *   dnu:  host double; d loss / d nu of this step is ADDED to it.
+ * The handle's state is not touched; its precision and tolerances apply to
+ * the four CG solves.  The first call allocates a work arena of
+ * (3 nsub + 7) dim + 5 fields.  Returns the first non-OK solve status. */
+int sdg_step_adjoint(sdg_handle* h, const double* const* U, double* const* lamU,
+                     double* lamP, double* dnu, void* stream);
+
 /* ---------------------------------------------------------------- batches */
 
 /* A batch of independent problems of uneven size and degree (each one the

@@ -539,7 +539,7 @@ int sdg_destroy(sdg_handle* h) {
   cudaFree(h->x32); cudaFree(h->r32); cudaFree(h->p32[0]); cudaFree(h->p32[1]); cudaFree(h->Ap32);
   cudaFree(h->st); cudaFree(h->partials); cudaFree(h->mats);
   cudaFree(h->x0buf); cudaFree(h->kpart); cudaFree(h->kcorr); cudaFree(h->kproj);
-  cudaFree(h->kbasis); cudaFree(h->kdpart); cudaFree(h->kc);
+  cudaFree(h->kbasis); cudaFree(h->kdpart); cudaFree(h->kc); cudaFree(h->adj);
   if (h->st_host) cudaFreeHost(h->st_host);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
@@ -748,6 +748,143 @@ int sdg_step(sdg_handle* h, int nsteps, sdg_step_info* info, void* stream) {
     info->pressure_applies = p_applies;
     info->kernel_launches = h->launches - launches0;
   }
+  return first_bad;
+}
+
+int sdg_step_adjoint(sdg_handle* h, const double* const* U, double* const* lamU, double* lamP, double* dnu,
+                     void* stream) {
+  SDG_ARG(h && U && lamU && lamP && dnu, "NULL argument");
+  for (int d = 0; d < h->dim; ++d) SDG_ARG(U[d] && lamU[d], "NULL component");
+  cudaStream_t s = S(stream);
+  const int D = h->dim, K = h->nsub;
+  const long long n = h->g.ndof;
+  const long long need = 3LL * K * D + 7LL * D + 5;
+  if (h->adj_fields < need) {
+    SDG_CK(cudaStreamSynchronize(s));
+    SDG_CK(cudaFree(h->adj));
+    h->adj = nullptr;
+    h->adj_fields = 0;
+    if (alloc(&h->adj, (size_t)(need * n)) != SDG_OK) return SDG_ERR_CUDA;
+    h->adj_fields = need;
+  }
+  long long next = 0;
+  auto field = [&]() { return h->adj + (next++) * n; };
+  std::vector<double*> stW(K * D), stS1(K * D), stS2(K * D);
+  for (int k = 0; k < K * D; ++k) {
+    stW[k] = field();
+    stS1[k] = field();
+    stS2[k] = field();
+  }
+  double *lx = field(), *kx = field(), *zero = field(), *lPo = field(), *mup = field();
+  double *lUs[3] = {nullptr, nullptr, nullptr}, *lVh[3] = {nullptr, nullptr, nullptr};
+  double *mu[3] = {nullptr, nullptr, nullptr}, *lam[3] = {nullptr, nullptr, nullptr};
+  double *lamW[3] = {nullptr, nullptr, nullptr}, *lamS1[3] = {nullptr, nullptr, nullptr};
+  double *lamS2[3] = {nullptr, nullptr, nullptr};
+  for (int d = 0; d < D; ++d) {
+    lUs[d] = field();
+    lVh[d] = field();
+    mu[d] = field();
+    lam[d] = field();
+    lamW[d] = field();
+    lamS1[d] = field();
+    lamS2[d] = field();
+  }
+  const size_t bytes = (size_t)n * sizeof(double);
+  const double kdt = h->dt / K;
+  int first_bad = SDG_OK;
+  auto note = [&](int rc) {
+    if (rc != SDG_OK && first_bad == SDG_OK) first_bad = rc;
+  };
+  SolverState* stm = st_dev(h, kStMisc);
+  double* pm = parts(h, kStMisc);
+
+  // ---- forward recompute of the step's convection stages and viscous solves
+  for (int d = 0; d < D; ++d) SDG_K(k_dual_to_main(h, d, U[d], stW[d], s));
+  for (int k = 0; k < K; ++k) {
+    const double* W[3] = {stW[k * D], D > 1 ? stW[k * D + 1] : nullptr, D > 2 ? stW[k * D + 2] : nullptr};
+    double* S1[3] = {stS1[k * D], D > 1 ? stS1[k * D + 1] : nullptr, D > 2 ? stS1[k * D + 2] : nullptr};
+    double* S2[3] = {stS2[k * D], D > 1 ? stS2[k * D + 1] : nullptr, D > 2 ? stS2[k * D + 2] : nullptr};
+    double* out[3];
+    for (int d = 0; d < 3; ++d) out[d] = (k + 1 < K) ? (d < D ? stW[(k + 1) * D + d] : nullptr) : h->F[d];
+    SDG_K(k_convect_stage(h, nullptr, W, S1, 0.0, 1.0, kdt, s));
+    SDG_K(k_convect_stage(h, W, S1, S2, 0.75, 0.25, kdt, s));
+    SDG_K(k_convect_stage(h, W, S2, out, 1.0 / 3.0, 2.0 / 3.0, kdt, s));
+  }
+  sdg_cg_info info{};
+  for (int c = 0; c < D; ++c) {
+    SDG_K(k_mass_rhs(h, h->F[c], h->b, h->Vh[c], s));
+    const int rc = solve(h, false, h->b, h->Vh[c], &info, s);
+    if (rc == SDG_ERR_CUDA || rc == SDG_ERR_INVALID_ARG) return rc;
+    note(rc);
+  }
+
+  // ---- velocity update and pressure (Eqs. LOvelocityU-W, LOpressure, gauge)
+  SDG_K(adj_velocity_T(h, lamU, lamP, lx, lPo, s));
+  SDG_K(adj_dot(lx, nullptr, n, stm, 0, pm, s));
+  SDG_K(adj_sub_weighted(h, lx, stm, 0, 1.0 / (double)h->g.ncell, s));
+  SDG_CK(cudaMemcpyAsync(kx, lx, bytes, cudaMemcpyDeviceToDevice, s));
+  SDG_CK(cudaMemsetAsync(zero, 0, bytes, s));
+  {
+    int nl = 0;
+    SDG_CK(kernel_restore(h, lx, zero, s, &nl));  // lx <- range part
+    h->launches += nl;
+  }
+  SDG_K(adj_axpby(kx, 1.0, kx, -1.0, lx, n, s));  // kernel part passes to P^n
+  SDG_K(adj_axpby(lPo, 1.0, lPo, 1.0, kx, n, s));
+  SDG_CK(cudaMemsetAsync(mup, 0, bytes, s));
+  {
+    const int rc = solve(h, true, lx, mup, &info, s);
+    if (rc == SDG_ERR_CUDA || rc == SDG_ERR_INVALID_ARG) return rc;
+    note(rc);
+  }
+  SDG_K(adj_dot(mup, nullptr, n, stm, 0, pm, s));
+  SDG_K(k_shift(mup, n, stm, 0, 1.0 / (double)n, s));  // lambda_b (zero mean)
+  SDG_K(adj_divergence_T(h, lamU, mup, lUs, s));
+  {
+    Op op{};
+    for (int d = 0; d < D; ++d) op.s[d] = (1.0 - h->theta) * h->dt / (h->dx[d] * h->dx[d]);
+    SDG_K(apply_plain<double>(h, op, mup, h->tmp, s));
+    SDG_K(adj_axpby(lPo, 1.0, lPo, -1.0, h->tmp, n, s));
+  }
+  // ---- projections back and the viscous solves (symmetric operator)
+  for (int d = 0; d < D; ++d) SDG_K(adj_project_T(h, false, d, lUs[d], lVh[d], s));
+  for (int c = 0; c < D; ++c) {
+    SDG_CK(cudaMemsetAsync(mu[c], 0, bytes, s));
+    const int rc = solve(h, false, lVh[c], mu[c], &info, s);
+    if (rc == SDG_ERR_CUDA || rc == SDG_ERR_INVALID_ARG) return rc;
+    note(rc);
+  }
+  // d/dnu: Vh = (M + nu A')^-1 M F  =>  - mu . A' Vh
+  {
+    Op op{};
+    for (int d = 0; d < D; ++d) op.s[d] = h->dt / (h->dx[d] * h->dx[d]);
+    double acc = 0.0;
+    for (int c = 0; c < D; ++c) {
+      SDG_K(apply_plain<double>(h, op, h->Vh[c], h->tmp, s));
+      SDG_K(adj_dot(mu[c], h->tmp, n, stm, 1, pm, s));
+      SDG_CK(cudaMemcpyAsync(h->st_host + kStMisc, stm, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+      SDG_CK(cudaStreamSynchronize(s));
+      acc += h->st_host[kStMisc].red[1];
+    }
+    *dnu -= acc;
+  }
+  for (int c = 0; c < D; ++c) SDG_K(k_mass_rhs(h, mu[c], lam[c], nullptr, s));  // lambda_F = M mu
+  // ---- SSP-RK3 sub-steps in reverse
+  for (int k = K - 1; k >= 0; --k) {
+    const double* W[3] = {stW[k * D], D > 1 ? stW[k * D + 1] : nullptr, D > 2 ? stW[k * D + 2] : nullptr};
+    const double* S1[3] = {stS1[k * D], D > 1 ? stS1[k * D + 1] : nullptr, D > 2 ? stS1[k * D + 2] : nullptr};
+    const double* S2[3] = {stS2[k * D], D > 1 ? stS2[k * D + 1] : nullptr, D > 2 ? stS2[k * D + 2] : nullptr};
+    const double* lamc[3] = {lam[0], lam[1], lam[2]};
+    const double* ls2[3] = {lamS2[0], lamS2[1], lamS2[2]};
+    const double* ls1[3] = {lamS1[0], lamS1[1], lamS1[2]};
+    const double* lw[3] = {lamW[0], lamW[1], lamW[2]};
+    SDG_K(adj_convect_T(h, S2, lamc, nullptr, lamS2, 0.0, 2.0 / 3.0, kdt, s));
+    for (int c = 0; c < D; ++c) SDG_K(adj_axpby(lamW[c], 1.0 / 3.0, lam[c], 0.75, lamS2[c], n, s));
+    SDG_K(adj_convect_T(h, S1, ls2, nullptr, lamS1, 0.0, 0.25, kdt, s));
+    SDG_K(adj_convect_T(h, W, ls1, lw, lam, 1.0, 1.0, kdt, s));
+  }
+  for (int d = 0; d < D; ++d) SDG_K(adj_project_T(h, true, d, lam[d], lamU[d], s));
+  SDG_CK(cudaMemcpyAsync(lamP, lPo, bytes, cudaMemcpyDeviceToDevice, s));
   return first_bad;
 }
 

@@ -92,6 +92,8 @@ struct sdg_handle {
   double* b;        // right-hand side
   double* Pn;       // new pressure
   double* tmp;      // scratch field
+  double* adj;      // adjoint work arena (allocated by the first sdg_step_adjoint)
+  long long adj_fields;  // fields of ndof doubles in adj
   // solver vectors
   // p is double-buffered: the fused apply reads p_old with its halo while
   // other CTAs write p_new, so the two must not alias.
@@ -220,5 +222,22 @@ cudaError_t k_weighted_sum(const sdg_handle* h, const double* x, const double* y
                            int slot, double* partials, cudaStream_t s);
 // st->red[slot] = sum x*x
 cudaError_t k_norm2(const double* x, long long n, SolverState* st, int slot, double* partials, cudaStream_t s);
+
+// adjoint of the step (transposed stages, FP64)
+cudaError_t adj_project_T(const sdg_handle* h, bool dual_to_main, int d, const double* lam, double* out,
+                          cudaStream_t s);
+cudaError_t adj_velocity_T(const sdg_handle* h, const double* const* lamU, const double* lamP, double* lx,
+                           double* lPo, cudaStream_t s);
+cudaError_t adj_divergence_T(const sdg_handle* h, const double* const* lamU, const double* lb, double* const* out,
+                             cudaStream_t s);
+cudaError_t adj_convect_T(const sdg_handle* h, const double* const* X, const double* const* lam,
+                          const double* const* base, double* const* out, double a, double b, double k,
+                          cudaStream_t s);
+cudaError_t adj_axpby(double* out, double a, const double* x, double b, const double* y, long long n,
+                      cudaStream_t s);
+cudaError_t adj_dot(const double* x, const double* y, long long n, SolverState* st, int slot, double* partials,
+                    cudaStream_t s);
+cudaError_t adj_sub_weighted(const sdg_handle* h, double* x, const SolverState* st, int slot, double factor,
+                             cudaStream_t s);
 
 }  // namespace sdg

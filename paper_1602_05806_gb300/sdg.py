@@ -31,7 +31,7 @@ EXPORTS = (
     "sdg_set_mixed_options", "sdg_set_convection_substeps", "sdg_ndof", "sdg_set_state", "sdg_get_state",
     "sdg_pressure_apply", "sdg_viscous_apply", "sdg_pressure_cg", "sdg_viscous_cg",
     "sdg_dual_to_main", "sdg_main_to_dual", "sdg_convect", "sdg_pressure_rhs",
-    "sdg_velocity_update", "sdg_step", "sdg_set_profiling", "sdg_counters", "sdg_diagnostics",
+    "sdg_velocity_update", "sdg_step", "sdg_step_adjoint", "sdg_set_profiling", "sdg_counters", "sdg_diagnostics",
     "sdg_kinetic_energy_noalloc", "sdg_batch_create", "sdg_batch_destroy", "sdg_batch_size",
     "sdg_batch_member", "sdg_batch_set_threads", "sdg_batch_step", "sdg_strerror", "sdg_last_error",
 )
@@ -105,6 +105,7 @@ def lib():
         L.sdg_strerror.argtypes = [ip]
         L.sdg_strerror.restype = ctypes.c_char_p
         L.sdg_last_error.restype = ctypes.c_char_p
+        L.sdg_step_adjoint.argtypes = [vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double), vp]
         L.sdg_batch_create.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp, ip, ctypes.c_double,
                                        ctypes.c_double, ctypes.POINTER(ctypes.c_void_p)]
         L.sdg_batch_destroy.argtypes = [vp]
@@ -303,6 +304,15 @@ class Handle:
                 "viscous": [info.viscous[c].as_dict() for c in range(self.dim)],
                 "pressure_ms": info.pressure_ms, "step_ms": info.step_ms,
                 "pressure_applies": info.pressure_applies, "kernel_launches": info.kernel_launches}
+
+    def step_adjoint(self, U, lamU, lamP, stream=None, ok=(SDG_OK,)):
+        """Adjoint of one step at the checkpoint U (start of the step):
+        lamU / lamP are updated in place from the cotangents of the step's
+        outputs to those of its inputs; returns d loss / d nu of the step."""
+        dnu = ctypes.c_double(0.0)
+        check(lib().sdg_step_adjoint(self.h, _ptr_array(U), _ptr_array(lamU), _ptr(lamP), ctypes.byref(dnu),
+                                     _stream(stream)), ok)
+        return dnu.value
 
     def diagnostics(self, stream=None):
         ke = ctypes.c_double()
