@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed plain-FP64 steps (after one warm-up)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tg3d-steps", type=int, default=1,
+                    help="timed steps of the 3D 48^3, N = 4 workload (after one warm-up); 0 skips it")
     ap.add_argument("--batch-steps", type=int, default=1,
                     help="timed steps of the 48-problem batch (after one warm-up); 0 skips it")
     return ap.parse_args()
@@ -376,6 +378,38 @@ def run_ours(args):
                "h2d_bytes_per_step": 3 * ndof * 8, "d2h_bytes_per_step": 3 * ndof * 8,
                "ms_per_step": 1000 * t_tot / args.e2e_steps}
 
+    # ---- 3D workload: 48^3 cells, N = 4 (block hepta-diagonal pressure system)
+    tg3d = None
+    if args.tg3d_steps > 0:
+        w3, U3, P3 = workload_state("tg3d_48_N4")
+        h3 = sdg.Handle(3, w3["n"], w3["L"], w3["N"], w3["nu"], w3["theta"], w3["dt"])
+        h3.set_convection_substeps(w3["nsub"])
+        res3 = {}
+        for prec, name in ((sdg.SDG_MIXED, "mixed"), (sdg.SDG_FP64, "fp64")):
+            h3.set_options(prec, 1e-12, 1e-12)
+            h3.set_state([dev(u) for u in U3], dev(P3))
+            assert h3.step(1)["status"] == sdg.SDG_OK  # warm-up
+            flush.fill_(0.25)
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            pms, app, its = 0.0, 0, []
+            for _ in range(args.tg3d_steps):
+                inf = h3.step(1)
+                assert inf["status"] == sdg.SDG_OK, inf
+                pms += inf["pressure_ms"]
+                app += inf["pressure_applies"]
+                its.append(inf["pressure"]["iters"])
+            e.record(stream)
+            torch.cuda.synchronize()
+            ke, _ = h3.diagnostics()
+            res3[name] = {"ms_per_step": a.elapsed_time(e) / args.tg3d_steps,
+                          "pressure_gdofs": h3.ndof * app / (pms * 1e-3) / 1e9, "pressure_iters": its,
+                          "kinetic_energy_after": ke}
+        tg3d = {"workload": "tg3d_48_N4 (3D TG, 48^3 cells, N 4, nu 1/1600, dt 1e-3, rtol 1e-12)",
+                "dof": h3.ndof, "steps": args.tg3d_steps, "warmup": 1, **res3}
+        h3.close()
+
     # ---- batched workload: 48 independent problems stepped concurrently
     batch = None
     if args.batch_steps > 0:
@@ -428,7 +462,7 @@ def run_ours(args):
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "pressure_iters_per_step": p_iters, "pressure_ms_total": p_ms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "fp64": fp64, "accuracy": accuracy, "batch": batch}
+                "clocks": clocks, "fp64": fp64, "accuracy": accuracy, "tg3d": tg3d, "batch": batch}
         print(json.dumps(line), flush=True)
     h.close()
     if dist is not None:
