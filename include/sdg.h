@@ -152,7 +152,21 @@ int sdg_set_mixed_options(sdg_handle* h, double delta, int max_updates, int defl
  * paper states it.  Errors: INVALID_ARG unless 1 <= nsub <= 1000. */
 int sdg_set_convection_substeps(sdg_handle* h, int nsub);
 
-/* Number of DOF of one field (ncell * n1^dim). */
+/* Tile shape of the 2D FP32 operator kernel (a CTA's box of elements):
+ * 0 = base, 1 = twice as wide in x, 2 = twice as wide in y (fewer halo
+ * loads per element, twice the threads per CTA).  Ignored in 3D.  The
+ * shape changes the summation order of the CG's dot products, so results
+ * differ in the last bits between shapes (each is deterministic).
+ * Errors: INVALID_ARG. */
+int sdg_set_tile(sdg_handle* h, int variant);
+/* Times the FP32 operator of the handle's grid with every tile shape (10
+ * launches each, CUDA events on `stream`), keeps the fastest and returns it
+ * in *variant (may be NULL); us (may be NULL) receives the mean launch time
+ * of each shape in microseconds (3 entries in 2D, 1 in 3D).  No counterpart
+ * in the paper: a tuning aid.  Synchronises the stream. */
+int sdg_autotune(sdg_handle* h, int* variant, double* us, void* stream);
+
+/* Number of DOF of one field (ncell * n1^dim). *//* Number of DOF of one field (ncell * n1^dim). */
 long long sdg_ndof(const sdg_handle* h);
 
 /* Copy the state in / out.  u, v (, w in 3D; NULL in 2D), p: host or device

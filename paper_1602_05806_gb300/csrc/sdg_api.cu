@@ -91,6 +91,7 @@ cudaError_t apply_plain(const sdg_handle* h, const Op& op, const T* x, T* y, cud
   for (int d = 0; d < 3; ++d) a.s[d] = op.s[d];
   a.cmass = op.cmass;
   a.fuse = 0;
+  a.tile = h->tile32;
   if constexpr (sizeof(T) == 8)
     return launch_apply_f64(h, a, s);
   else
@@ -147,6 +148,7 @@ int cg_loop(sdg_handle* h, const Op& op, T* x, T* r, T* const* p, T* Ap, int sid
       a.st = st;
       a.partials = pa;
       a.kc = deflate ? h->kc : nullptr;
+      a.tile = h->tile32;
       if (prof) SDG_CK(cudaEventRecord(h->pev[2 * k], s));
       if constexpr (sizeof(T) == 8) {
         SDG_K(launch_apply_f64(h, a, s));
@@ -429,6 +431,7 @@ int sdg_create(const sdg_grid* grid, int N, double nu, double theta, double dt, 
   h->rtol_p = h->rtol_v = 1e-12;
   h->delta = 0.1;
   h->nsub = 1;
+  h->tile32 = 0;
   h->maxit = 1000000;
   h->max_updates = 1000;
   build_basis(N, &h->basis);
@@ -577,6 +580,42 @@ int sdg_set_convection_substeps(sdg_handle* h, int nsub) {
   SDG_ARG(h, "NULL handle");
   SDG_ARG(nsub >= 1 && nsub <= 1000, "nsub must be in [1, 1000]");
   h->nsub = nsub;
+  return SDG_OK;
+}
+
+int sdg_set_tile(sdg_handle* h, int variant) {
+  SDG_ARG(h, "NULL handle");
+  SDG_ARG(variant >= 0 && variant <= 2, "tile variant must be 0, 1 or 2");
+  h->tile32 = h->dim == 2 ? variant : 0;
+  return SDG_OK;
+}
+
+int sdg_autotune(sdg_handle* h, int* variant, double* us, void* stream) {
+  SDG_ARG(h, "NULL handle");
+  cudaStream_t s = S(stream);
+  const int nv = h->dim == 2 ? 3 : 1;
+  Op op = pressure_op(h);
+  double best = 1e300;
+  int pick = 0;
+  for (int v = 0; v < nv; ++v) {
+    h->tile32 = v;
+    for (int k = 0; k < 3; ++k) SDG_K(apply_plain<float>(h, op, h->p32[0], h->Ap32, s));
+    SDG_CK(cudaEventRecord(h->ev0, s));
+    constexpr int kReps = 10;
+    for (int k = 0; k < kReps; ++k) SDG_K(apply_plain<float>(h, op, h->p32[0], h->Ap32, s));
+    SDG_CK(cudaEventRecord(h->ev1, s));
+    SDG_CK(cudaEventSynchronize(h->ev1));
+    float ms = 0.f;
+    SDG_CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    const double t = 1e3 * ms / kReps;
+    if (us) us[v] = t;
+    if (t < best) {
+      best = t;
+      pick = v;
+    }
+  }
+  h->tile32 = pick;
+  if (variant) *variant = pick;
   return SDG_OK;
 }
 

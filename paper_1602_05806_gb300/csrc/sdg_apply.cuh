@@ -24,13 +24,17 @@ namespace sdg {
 
 __host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 
-// Element box per CTA for each (dim, n1): about 200-300 threads (one per line).
-template <int DIM, int N1>
+// Element box per CTA for each (dim, n1): about 200-300 threads (one per
+// line) for the base shape V = 0; in 2D, V = 1 doubles the box along x and
+// V = 2 along y (fewer halo loads per element, twice the threads).
+template <int DIM, int N1, int V = 0>
 struct Tile {
-  static constexpr int TX = DIM == 2 ? (N1 <= 1 ? 16 : N1 <= 2 ? 16 : N1 <= 4 ? 8 : N1 <= 8 ? 8 : 4)
+  static constexpr int BX = DIM == 2 ? (N1 <= 1 ? 16 : N1 <= 2 ? 16 : N1 <= 4 ? 8 : N1 <= 8 ? 8 : 4)
                                      : (N1 <= 1 ? 8 : N1 <= 2 ? 4 : N1 <= 3 ? 4 : N1 <= 4 ? 4 : N1 <= 10 ? 2 : 1);
-  static constexpr int TY = DIM == 2 ? (N1 <= 1 ? 16 : N1 <= 2 ? 8 : N1 <= 4 ? 8 : N1 <= 8 ? 4 : 4)
+  static constexpr int BY = DIM == 2 ? (N1 <= 1 ? 16 : N1 <= 2 ? 8 : N1 <= 4 ? 8 : N1 <= 8 ? 4 : 4)
                                      : (N1 <= 1 ? 8 : N1 <= 2 ? 4 : N1 <= 3 ? 4 : N1 <= 4 ? 2 : N1 <= 8 ? 2 : 1);
+  static constexpr int TX = BX * ((DIM == 2 && V == 1) ? 2 : 1);
+  static constexpr int TY = BY * ((DIM == 2 && V == 2) ? 2 : 1);
   static constexpr int TZ = DIM == 2 ? 1
                                      : (N1 <= 1 ? 4 : N1 <= 2 ? 4 : N1 <= 3 ? 2 : N1 <= 4 ? 2 : N1 <= 5 ? 2 : 1);
   static constexpr int TE = TX * TY * TZ;
@@ -151,17 +155,18 @@ __device__ __forceinline__ bool slot_elem(int s, const int o[3], int VX, int VY,
 // used for every FP32 application and for the FP64 true residuals of the
 // mixed solver; plain FP64 CG uses the direct contraction.
 // Blocks per SM the kernel is compiled for (register cap).  2D FP32 with
-// n1 = 8 fits 40 registers without spills, so six 256-thread blocks share
-// an SM (as its shared-memory tile allows); elsewhere the compiler chooses.
-template <typename T, int DIM, int N1>
+// n1 = 8 fits 40 registers without spills, so six 256-thread blocks (three
+// of the 512-thread shapes) share an SM, as the shared-memory tile allows;
+// elsewhere the compiler chooses.
+template <typename T, int DIM, int N1, int V>
 constexpr int apply_min_blocks() {
-  return (sizeof(T) == 4 && DIM == 2 && N1 == 8) ? 6 : 1;
+  return (sizeof(T) == 4 && DIM == 2 && N1 == 8) ? (V == 0 ? 6 : 3) : 1;
 }
 
-template <typename T, int DIM, int N1, bool ACC>
-__global__ void __launch_bounds__(Tile<DIM, N1>::THREADS, (apply_min_blocks<T, DIM, N1>()))
+template <typename T, int DIM, int N1, bool ACC, int TV>
+__global__ void __launch_bounds__(Tile<DIM, N1, TV>::THREADS, (apply_min_blocks<T, DIM, N1, TV>()))
     k_apply(const __grid_constant__ ApplyParams<T, DIM, N1> a) {
-  using TS = Tile<DIM, N1>;
+  using TS = Tile<DIM, N1, TV>;
   constexpr int TX = TS::TX, TY = TS::TY, TZ = TS::TZ, TE = TS::TE;
   constexpr int NPE = TS::NPE, LINES = TS::LINES, NSLOT = TS::NSLOT;
   constexpr int VW = Vec<T, NPE>::W;
@@ -476,9 +481,9 @@ __global__ void __launch_bounds__(Tile<DIM, N1>::THREADS, (apply_min_blocks<T, D
   }
 }
 
-template <typename T, int DIM, int N1, bool ACC>
+template <typename T, int DIM, int N1, bool ACC, int V>
 cudaError_t launch_apply_acc(const sdg_handle* h, const ApplyArgs<T>& in, cudaStream_t stream) {
-  using TS = Tile<DIM, N1>;
+  using TS = Tile<DIM, N1, V>;
   ApplyParams<T, DIM, N1> p;
   const Basis1D& b = h->basis;
   const CoefSet& cs = sizeof(T) == 4 ? h->coef32 : h->coef64;  // values exact in T
@@ -532,22 +537,28 @@ cudaError_t launch_apply_acc(const sdg_handle* h, const ApplyArgs<T>& in, cudaSt
   // harmless
   static std::atomic<bool> attr_set{false};
   if (!attr_set.load(std::memory_order_acquire)) {
-    cudaError_t e = cudaFuncSetAttribute(k_apply<T, DIM, N1, ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_apply<T, DIM, N1, ACC, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     attr_set.store(true, std::memory_order_release);
   }
-  k_apply<T, DIM, N1, ACC><<<(unsigned)nblk, TS::THREADS, smem, stream>>>(p);
+  k_apply<T, DIM, N1, ACC, V><<<(unsigned)nblk, TS::THREADS, smem, stream>>>(p);
   return cudaGetLastError();
 }
 
+// Tile shape variants exist for the 2D FP32 operator only (the FP64 one is
+// bound by the FP64 pipe, not by the tile).
 template <typename T, int DIM, int N1>
 cudaError_t launch_apply_t(const sdg_handle* h, const ApplyArgs<T>& in, cudaStream_t stream) {
   if constexpr (sizeof(T) == 4) {
-    return launch_apply_acc<T, DIM, N1, true>(h, in, stream);
+    if constexpr (DIM == 2) {
+      if (in.tile == 1) return launch_apply_acc<T, DIM, N1, true, 1>(h, in, stream);
+      if (in.tile == 2) return launch_apply_acc<T, DIM, N1, true, 2>(h, in, stream);
+    }
+    return launch_apply_acc<T, DIM, N1, true, 0>(h, in, stream);
   } else {
-    if (in.accurate) return launch_apply_acc<T, DIM, N1, true>(h, in, stream);
-    return launch_apply_acc<T, DIM, N1, false>(h, in, stream);
+    if (in.accurate) return launch_apply_acc<T, DIM, N1, true, 0>(h, in, stream);
+    return launch_apply_acc<T, DIM, N1, false, 0>(h, in, stream);
   }
 }
 

@@ -70,6 +70,7 @@ struct sdg_handle {
   double L[3], dx[3];
   double nu, theta, dt;
   int nsub;                      // SSP-RK3 sub-steps of the explicit convection per dt
+  int tile32;                    // tile shape variant of the 2D FP32 operator
   int precision;
   double rtol_p, rtol_v;
   double delta;     // mixed: reliable-update factor
@@ -162,6 +163,7 @@ struct ApplyArgs {
   double* partials;
   const float* kc;  // fuse = 1, FP32: subtract kc (per local node) from r; null = off
   int accurate;     // FP64: use the accurate contraction (FP32 always does)
+  int tile;         // 2D FP32: tile shape variant (0 base, 1 wide in x, 2 wide in y)
 };
 
 cudaError_t launch_apply_f64(const sdg_handle* h, const ApplyArgs<double>& a, cudaStream_t s);

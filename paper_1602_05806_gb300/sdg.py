@@ -28,7 +28,7 @@ SDG_MIXED = 1
 # every symbol include/sdg.h declares
 EXPORTS = (
     "sdg_nodes", "sdg_matrices", "sdg_kernel_projector", "sdg_line_operator", "sdg_create", "sdg_destroy", "sdg_set_options",
-    "sdg_set_mixed_options", "sdg_set_convection_substeps", "sdg_ndof", "sdg_set_state", "sdg_get_state",
+    "sdg_set_mixed_options", "sdg_set_convection_substeps", "sdg_set_tile", "sdg_autotune", "sdg_ndof", "sdg_set_state", "sdg_get_state",
     "sdg_pressure_apply", "sdg_viscous_apply", "sdg_pressure_cg", "sdg_viscous_cg",
     "sdg_dual_to_main", "sdg_main_to_dual", "sdg_convect", "sdg_pressure_rhs",
     "sdg_velocity_update", "sdg_step", "sdg_step_adjoint", "sdg_set_profiling", "sdg_counters", "sdg_diagnostics",
@@ -83,6 +83,8 @@ def lib():
         L.sdg_set_options.argtypes = [vp, ip, ctypes.c_double, ctypes.c_double, ip]
         L.sdg_set_mixed_options.argtypes = [vp, ctypes.c_double, ip, ip]
         L.sdg_set_convection_substeps.argtypes = [vp, ip]
+        L.sdg_set_tile.argtypes = [vp, ip]
+        L.sdg_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp, vp]
         L.sdg_ndof.argtypes = [vp]
         L.sdg_ndof.restype = ctypes.c_longlong
         L.sdg_set_state.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -137,9 +139,13 @@ def _ptr(t):
 
 
 def _stream(stream):
+    """CUDA stream handle: the current torch stream (None), a torch.cuda.Stream,
+    or a raw handle."""
     if stream is None:
         import torch
         return torch.cuda.current_stream().cuda_stream
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
     return int(stream)
 
 
@@ -242,6 +248,17 @@ class Handle:
     def set_convection_substeps(self, nsub):
         """SSP-RK3 sub-steps of the explicit convection per time step."""
         check(lib().sdg_set_convection_substeps(self.h, int(nsub)))
+
+    def set_tile(self, variant):
+        """Tile shape of the 2D FP32 operator (0 base, 1 wide in x, 2 wide in y)."""
+        check(lib().sdg_set_tile(self.h, int(variant)))
+
+    def autotune(self, stream=None):
+        """(chosen tile variant, mean launch time in us of every variant)."""
+        v = ctypes.c_int()
+        us = (ctypes.c_double * 3)()
+        check(lib().sdg_autotune(self.h, ctypes.byref(v), us, _stream(stream)))
+        return v.value, [us[i] for i in range(3 if self.dim == 2 else 1)]
 
     def set_profiling(self, enable=True):
         check(lib().sdg_set_profiling(self.h, 1 if enable else 0))

@@ -111,6 +111,33 @@ def test_pressure_cg_mixed(dim, n, N):
     assert rel(xg, ref.x) <= 1e-10
 
 
+@pytest.mark.parametrize("N", [1, 3, 7, 10])
+def test_tile_variants_apply_and_mixed_cg(N):
+    """Every tile shape of the 2D FP32 operator (base, wide in x, wide in y)
+    on a grid that leaves ragged boxes in both directions: the FP32 operator
+    against the oracle, and a mixed-precision pressure solve to 1e-13.  The
+    tuner returns one of the shapes and a time for each."""
+    o, h = make(2, (19, 13), N, L=(1.3, 2.1))
+    rng = np.random.default_rng(40 + N)
+    x32 = rng.standard_normal(o.shape).astype(np.float32)
+    ref = o.pressure_apply(x32.astype(np.float64))
+    b = o.pressure_apply(rng.standard_normal(o.shape))
+    x0 = rng.standard_normal(o.shape)
+    X32 = dev(x32, torch.float32)
+    Y32 = torch.empty_like(X32)
+    h.set_options(sdg.SDG_MIXED, 1e-13, 1e-13, 1000000)
+    for v in range(3):
+        h.set_tile(v)
+        h.pressure_apply(X32, Y32)
+        assert rel(host(Y32), ref) <= 2e-5, v
+        B, X = dev(b), dev(x0)
+        info = h.pressure_cg(B, X)
+        assert info["status"] == sdg.SDG_OK, (v, info)
+        assert np.linalg.norm(b - o.pressure_apply(host(X))) <= 1e-13 * np.linalg.norm(b) * 1.01, v
+    best, us = h.autotune()
+    assert best in (0, 1, 2) and len(us) == 3 and min(us) > 0.0
+
+
 def test_viscous_cg_fp64_and_mixed():
     o, h = make(2, (7, 9), 4, nu=0.3)
     rng = np.random.default_rng(3)
