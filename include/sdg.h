@@ -244,8 +244,9 @@ int sdg_velocity_update(sdg_handle* h, const double* const* Ustar,
 
 /* Advance the handle's state by nsteps steps of the compact fractional-step
  * scheme (Eqs. LOdiffusionU-W, LOpressure, LOvelocityU-W): project to the
- * main grid, SSP-RK3 convection, implicit viscous CG per component, project
- * back, pressure CG, velocity update, pressure gauge (zero mean).
+ * main grid, SSP-RK3 convection (in sdg_set_convection_substeps sub-steps),
+ * implicit viscous CG per component, project back, pressure CG, velocity
+ * update, pressure gauge (zero mean).
  * info may be NULL.  Returns the first non-OK solve status, or OK. */
 int sdg_step(sdg_handle* h, int nsteps, sdg_step_info* info, void* stream);
 

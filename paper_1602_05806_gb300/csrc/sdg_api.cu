@@ -149,6 +149,7 @@ int cg_loop(sdg_handle* h, const Op& op, T* x, T* r, T* const* p, T* Ap, int sid
       a.partials = pa;
       a.kc = deflate ? h->kc : nullptr;
       a.tile = h->tile32;
+      a.pdl = prof ? 0 : 1;
       if (prof) SDG_CK(cudaEventRecord(h->pev[2 * k], s));
       if constexpr (sizeof(T) == 8) {
         SDG_K(launch_apply_f64(h, a, s));

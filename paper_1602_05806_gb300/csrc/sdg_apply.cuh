@@ -183,16 +183,10 @@ __global__ void __launch_bounds__(Tile<DIM, N1, TV>::THREADS, (apply_min_blocks<
 
   const bool fuse = a.fuse != 0;
   const bool defl = sizeof(T) == 4 && fuse && a.kc != nullptr;
-  bool first = false;
-  T beta = T(0);
-  if (fuse) {
-    if (a.st->done || a.st->pause) return;  // uniform: written by the previous kernel
-    first = (a.st->iter == 0);
-    // beta was formed once by the previous kernel (no FP64 division per thread)
-    if (!first) beta = sizeof(T) == 4 ? (T)a.st->beta_f : (T)a.st->beta;
-  }
+  pdl_trigger();
 
-  // tile origin and valid extents
+  // prologue that reads nothing earlier kernels write: tile origin and valid
+  // extents, weights, slot table (overlaps the previous kernel's tail)
   const int bx = blockIdx.x % a.ntile[0];
   const int by = (blockIdx.x / a.ntile[0]) % a.ntile[1];
   const int bz = blockIdx.x / (a.ntile[0] * a.ntile[1]);
@@ -202,14 +196,24 @@ __global__ void __launch_bounds__(Tile<DIM, N1, TV>::THREADS, (apply_min_blocks<
   const int VZ = DIM == 3 ? min(TZ, a.n[2] - o[2]) : 1;
 
   if (threadIdx.x < N1) s_w[threadIdx.x] = a.w[threadIdx.x];
-  if (defl)
-    for (int l = threadIdx.x; l < NPE; l += blockDim.x) s_kc[l] = (T)a.kc[l];
   for (int sl = threadIdx.x; sl < NSLOT; sl += blockDim.x) {
     int g[3];
     s_gel[sl] = slot_elem<DIM, TX, TY, TZ>(sl, o, VX, VY, VZ, a.n, g)
                     ? (int)(((long long)g[2] * a.n[1] + g[1]) * a.n[0] + g[0])
                     : -1;
   }
+
+  pdl_wait();
+  bool first = false;
+  T beta = T(0);
+  if (fuse) {
+    if (a.st->done || a.st->pause) return;  // uniform: written by the previous kernel
+    first = (a.st->iter == 0);
+    // beta was formed once by the previous kernel (no FP64 division per thread)
+    if (!first) beta = sizeof(T) == 4 ? (T)a.st->beta_f : (T)a.st->beta;
+  }
+  if (defl)
+    for (int l = threadIdx.x; l < NPE; l += blockDim.x) s_kc[l] = (T)a.kc[l];
   __syncthreads();
 
   // ---- stage box + face halo (coalesced vector loads, padded rows) ----
@@ -542,7 +546,18 @@ cudaError_t launch_apply_acc(const sdg_handle* h, const ApplyArgs<T>& in, cudaSt
     if (e != cudaSuccess) return e;
     attr_set.store(true, std::memory_order_release);
   }
-  k_apply<T, DIM, N1, ACC, V><<<(unsigned)nblk, TS::THREADS, smem, stream>>>(p);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)nblk);
+  cfg.blockDim = dim3(TS::THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = in.pdl ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_apply<T, DIM, N1, ACC, V>, p);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

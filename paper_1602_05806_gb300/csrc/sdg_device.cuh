@@ -160,6 +160,16 @@ __device__ __forceinline__ bool grid_sum_f2(F2 (&v)[K], double* partials, unsign
   return true;
 }
 
+// ---- programmatic dependent launch -----------------------------------------
+// A kernel launched with programmatic stream serialisation may start while
+// the previous kernel of the stream finishes.  pdl_trigger lets the next
+// kernel start (once every block of this one has called it); pdl_wait blocks
+// until the previous kernel has completed and its memory is visible, and
+// returns at once when the launch did not ask for the overlap.  Nothing that
+// an earlier kernel writes may be read, and nothing written, before pdl_wait.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ---- layout ----------------------------------------------------------------
 __device__ __forceinline__ void split_index(const Geo& g, long long idx, int e[3], int l[3]) {
   const long long el = idx / g.npe;

@@ -164,6 +164,7 @@ struct ApplyArgs {
   const float* kc;  // fuse = 1, FP32: subtract kc (per local node) from r; null = off
   int accurate;     // FP64: use the accurate contraction (FP32 always does)
   int tile;         // 2D FP32: tile shape variant (0 base, 1 wide in x, 2 wide in y)
+  int pdl;          // launch with programmatic stream serialisation (CG loop)
 };
 
 cudaError_t launch_apply_f64(const sdg_handle* h, const ApplyArgs<double>& a, cudaStream_t s);

@@ -16,6 +16,26 @@ inline unsigned grid_for(long long n) {
   return (unsigned)b;
 }
 
+// Launch with programmatic stream serialisation (the kernel may start while
+// the previous kernel of the stream finishes; see pdl_wait).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args...);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
 // grid of the vectorised CG update: enough blocks to fill the machine
 inline unsigned grid_vec(long long n, int w) {
   long long b = (n / w + kThreads - 1) / kThreads;
@@ -113,6 +133,8 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_cg_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ Ap,
                 long long n, SolverState* st, double* partials, Deflate df) {
+  pdl_trigger();
+  pdl_wait();  // alpha and Ap come from the operator kernel just before
   if (st->done || st->pause) return;
   extern __shared__ double s_dyn[];  // (deflation only)
   float* s_k = reinterpret_cast<float*>(s_dyn);  // npe floats (deflation)
@@ -692,15 +714,12 @@ cudaError_t cg_init_f32(const float* b, const float* Ax, float* r, long long n, 
 }
 cudaError_t cg_update_f64(double* x, double* r, const double* p, const double* Ap, long long n,
                           SolverState* st, double* partials, cudaStream_t s) {
-  k_cg_update<double><<<grid_vec(n, 2), kThreads, 0, s>>>(x, r, p, Ap, n, st, partials, Deflate{});
-  return cudaGetLastError();
+  return launch_pdl(k_cg_update<double>, grid_vec(n, 2), kThreads, 0, s, x, r, p, Ap, n, st, partials, Deflate{});
 }
 cudaError_t cg_update_f32(float* x, float* r, const float* p, const float* Ap, long long n,
                           SolverState* st, double* partials, const Deflate& df, cudaStream_t s) {
-  if (df.kpart == nullptr) {
-    k_cg_update<float><<<grid_vec(n, 4), kThreads, 0, s>>>(x, r, p, Ap, n, st, partials, df);
-    return cudaGetLastError();
-  }
+  if (df.kpart == nullptr)
+    return launch_pdl(k_cg_update<float>, grid_vec(n, 4), kThreads, 0, s, x, r, p, Ap, n, st, partials, df);
   const int npe = df.npe;
   const int G = kThreads >= 2 * npe ? kThreads / npe : 1;
   size_t smem = (size_t)(G + 1) * npe * sizeof(double);
