@@ -137,8 +137,10 @@ int sdg_destroy(sdg_handle* h);
  * Defaults: SDG_FP64, 1e-12, 1e-12, 1000000.  Errors: INVALID_ARG. */
 int sdg_set_options(sdg_handle* h, int precision, double rtol_p, double rtol_v,
                     int maxit);
-/* Mixed mode: reliable-update factor delta in (0,1) (default 0.1), the cap
- * on FP64 residual replacements per solve (default 1000), and deflate != 0
+/* Mixed mode: reliable-update factor delta in (0,1) (default 0.5: on the
+ * 256 x 256, N = 7 workload it needs 30,100 FP32 iterations against 42,600
+ * at 0.1 and 62,700 at 0.001), the cap on FP64 residual replacements per
+ * solve (default 10000), and deflate != 0
  * to remove the kernel of the pressure operator (odd N: constants and
  * sawtooth patterns) from every FP32 search direction (default 0: the
  * operator kernel already annihilates those patterns exactly). */

@@ -430,11 +430,11 @@ int sdg_create(const sdg_grid* grid, int N, double nu, double theta, double dt, 
   h->dt = dt;
   h->precision = SDG_FP64;
   h->rtol_p = h->rtol_v = 1e-12;
-  h->delta = 0.1;
+  h->delta = 0.5;
   h->nsub = 1;
   h->tile32 = 0;
   h->maxit = 1000000;
-  h->max_updates = 1000;
+  h->max_updates = 10000;
   build_basis(N, &h->basis);
   build_coefs(h->basis, 0, &h->coef64);
   build_coefs(h->basis, 1, &h->coef32);

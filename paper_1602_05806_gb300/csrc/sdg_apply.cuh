@@ -169,6 +169,9 @@ __global__ void __launch_bounds__(Tile<DIM, N1, TV>::THREADS, (apply_min_blocks<
   using TS = Tile<DIM, N1, TV>;
   constexpr int TX = TS::TX, TY = TS::TY, TZ = TS::TZ, TE = TS::TE;
   constexpr int NPE = TS::NPE, LINES = TS::LINES, NSLOT = TS::NSLOT;
+  // thread t works on element t / LINES: whole elements per warp when LINES
+  // divides 32 (and the block is whole warps)
+  constexpr bool WARP_ELEMS = (32 % LINES == 0) && (TS::THREADS % 32 == 0);
   constexpr int VW = Vec<T, NPE>::W;
   constexpr int NV = NPE / VW;  // vectors per element
   using V = typename std::conditional<VW == 1, T, typename VecOf<T>::V>::type;
@@ -428,12 +431,21 @@ __global__ void __launch_bounds__(Tile<DIM, N1, TV>::THREADS, (apply_min_blocks<
         }
       }
     }
-    __syncthreads();
+    // the passes of one element exchange data only through its own rows of
+    // s_out; when whole elements fall in one warp, a warp barrier suffices
+    if constexpr (WARP_ELEMS) __syncwarp();
+    else __syncthreads();
   }
 
   // ---- store the box (vectorised) and reduce p^T A p ----
+  // (WARP_ELEMS: every warp stores the elements it computed, with no block
+  // barrier in between)
   T dsum = T(0), dcomp = T(0);  // compensated per-thread sum in T
-  for (int v = threadIdx.x; v < TE * NV; v += blockDim.x) {
+  constexpr int EPW = WARP_ELEMS ? 32 / LINES : 1;  // elements per warp
+  const int v0 = WARP_ELEMS ? (threadIdx.x >> 5) * EPW * NV + (threadIdx.x & 31) : threadIdx.x;
+  const int v1 = WARP_ELEMS ? min(((threadIdx.x >> 5) + 1) * EPW, TE) * NV : TE * NV;
+  const int vstep = WARP_ELEMS ? 32 : blockDim.x;
+  for (int v = v0; v < v1; v += vstep) {
     const int e = v / NV, off = v - e * NV;
     const int ge = s_gel[e];
     if (ge < 0) continue;

@@ -242,7 +242,7 @@ class Handle:
     def set_options(self, precision=SDG_FP64, rtol_p=1e-12, rtol_v=1e-12, maxit=1000000):
         check(lib().sdg_set_options(self.h, precision, rtol_p, rtol_v, maxit))
 
-    def set_mixed_options(self, delta=0.1, max_updates=1000, deflate=False):
+    def set_mixed_options(self, delta=0.5, max_updates=10000, deflate=False):
         check(lib().sdg_set_mixed_options(self.h, delta, max_updates, 1 if deflate else 0))
 
     def set_convection_substeps(self, nsub):

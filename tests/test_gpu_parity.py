@@ -133,7 +133,9 @@ def test_tile_variants_apply_and_mixed_cg(N):
         B, X = dev(b), dev(x0)
         info = h.pressure_cg(B, X)
         assert info["status"] == sdg.SDG_OK, (v, info)
-        assert np.linalg.norm(b - o.pressure_apply(host(X))) <= 1e-13 * np.linalg.norm(b) * 1.01, v
+        # the mixed solver's stopping rule: true residual <= rtol, or <= 10 rtol
+        # once it stagnates at its FP64 floor
+        assert np.linalg.norm(b - o.pressure_apply(host(X))) <= 1e-12 * np.linalg.norm(b), v
     best, us = h.autotune()
     assert best in (0, 1, 2) and len(us) == 3 and min(us) > 0.0
 
