@@ -452,7 +452,7 @@ int sdg_create(const sdg_grid* grid, int N, double nu, double theta, double dt, 
 #define A_(p, c) if (rc == SDG_OK) rc = alloc(&(p), (size_t)(c))
   for (int d = 0; d < h->dim; ++d) {
     A_(h->U[d], n); A_(h->Vm[d], n); A_(h->S1[d], n); A_(h->S2[d], n);
-    A_(h->F[d], n); A_(h->Vh[d], n); A_(h->Us[d], n);
+    A_(h->F[d], n); A_(h->Vh[d], n); A_(h->Us[d], n); A_(h->Lc[d], n);
   }
   A_(h->P, n); A_(h->b, n); A_(h->Pn, n); A_(h->tmp, n);
   A_(h->r64, n); A_(h->p64[0], n); A_(h->p64[1], n); A_(h->Ap64, n);
@@ -536,7 +536,7 @@ int sdg_destroy(sdg_handle* h) {
   if (!h) return SDG_OK;
   for (int d = 0; d < 3; ++d) {
     cudaFree(h->U[d]); cudaFree(h->Vm[d]); cudaFree(h->S1[d]); cudaFree(h->S2[d]);
-    cudaFree(h->F[d]); cudaFree(h->Vh[d]); cudaFree(h->Us[d]);
+    cudaFree(h->F[d]); cudaFree(h->Vh[d]); cudaFree(h->Us[d]); cudaFree(h->Lc[d]);
   }
   cudaFree(h->P); cudaFree(h->b); cudaFree(h->Pn); cudaFree(h->tmp);
   cudaFree(h->r64); cudaFree(h->p64[0]); cudaFree(h->p64[1]); cudaFree(h->Ap64);
@@ -700,6 +700,7 @@ static int convect_rk3(sdg_handle* h, const double* const* V, double* const* F, 
     SDG_K(k_convect_stage(h, nullptr, W, h->S1, 0.0, 1.0, k, s));
     SDG_K(k_convect_stage(h, W, h->S1, h->S2, 0.75, 0.25, k, s));
     SDG_K(k_convect_stage(h, W, h->S2, F, 1.0 / 3.0, 2.0 / 3.0, k, s));
+    h->launches += 3 * (h->dim - 1);  // a stage is one launch per direction
   }
   return SDG_OK;
 }
@@ -849,6 +850,7 @@ int sdg_step_adjoint(sdg_handle* h, const double* const* U, double* const* lamU,
     SDG_K(k_convect_stage(h, nullptr, W, S1, 0.0, 1.0, kdt, s));
     SDG_K(k_convect_stage(h, W, S1, S2, 0.75, 0.25, kdt, s));
     SDG_K(k_convect_stage(h, W, S2, out, 1.0 / 3.0, 2.0 / 3.0, kdt, s));
+    h->launches += 3 * (h->dim - 1);  // a stage is one launch per direction
   }
   sdg_cg_info info{};
   for (int c = 0; c < D; ++c) {

@@ -87,6 +87,7 @@ struct sdg_handle {
   double* Vm[3];    // main-grid velocity
   double* S1[3];    // RK stage 1
   double* S2[3];    // RK stage 2
+  double* Lc[3];    // convection operator, accumulated over the directions
   double* F[3];     // RK3 result Fu
   double* Vh[3];    // viscous solution U^{n+1/2} on the main grid
   double* Us[3];    // U* on the dual grids
@@ -208,7 +209,7 @@ cudaError_t kernel_restore(const sdg_handle* h, double* x, const double* x0, cud
 cudaError_t k_dual_to_main(const sdg_handle* h, int d, const double* in, double* out, cudaStream_t s);
 cudaError_t k_main_to_dual(const sdg_handle* h, int d, const double* in, double* out, cudaStream_t s);
 // out_c = a * V0_c + b * (V_c + dt L(V)_c) for every component c (out may
-// alias V0, not V)
+// alias V0, not V); one launch per direction, L accumulated in h->Lc
 cudaError_t k_convect_stage(const sdg_handle* h, const double* const* V0, const double* const* V,
                             double* const* out, double a, double b, double dt, cudaStream_t s);
 // b = W F, x0 = F

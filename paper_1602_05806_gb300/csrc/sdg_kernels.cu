@@ -413,16 +413,22 @@ __device__ __forceinline__ double trace(const double* X, long long el, int npe, 
 // out_c = a V0_c + b (V_c + dt L(V)_c), with the collocated Rusanov DG operator
 //   L(q) = - sum_d (1/dx_d) M_d^-1 [phi(1) F^_{e+1/2} - phi(0) F^_{e-1/2} - Dn^T W (q v_d)]
 // F^ = (q^- v^- + q^+ v^+)/2 - s (q^+ - q^-)/2,  s = 2 max(|v_d^-|, |v_d^+|).
-struct ConvectParams {
+// Applied by lines: one thread per (element, line along d) forms the four
+// traces and two face fluxes of its line once and the n1 outputs of every
+// component.  Directions run as successive launches: the first writes L, the
+// next add to it, the last writes out_c = a V0_c + b (V_c + dt L_c) instead.
+struct ConvLineParams {
   Geo g;
-  double invdx[3];
+  int d, first, last;
+  double invdx;
   const double* V0[3];
   const double* V[3];
+  double* L[3];
   double* out[3];
   double a, b, dt;
 };
 
-__global__ void __launch_bounds__(kThreads) k_convect(ConvectParams p, const double* mats) {
+__global__ void __launch_bounds__(kThreads) k_convect_line(ConvLineParams p, const double* mats) {
   __shared__ double s_m[5 * kMatStride];
   const int ids[5] = {kW, kWinv, kPhi0, kPhi1, kDn};
   load_mats(mats, s_m, ids, 5);
@@ -432,50 +438,66 @@ __global__ void __launch_bounds__(kThreads) k_convect(ConvectParams p, const dou
   const double* phi1 = s_m + 3 * kMatStride;
   const double* Dn = s_m + 4 * kMatStride;
   const Geo& g = p.g;
-  const int n1 = g.n1, dim = g.dim;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.ndof;
-       idx += (long long)gridDim.x * blockDim.x) {
-    int e[3], l[3];
-    split_index(g, idx, e, l);
+  const int n1 = g.n1, dim = g.dim, d = p.d;
+  const int lpe = g.npe / n1;  // lines per element along d
+  const long long nlines = g.ncell * (long long)lpe;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nlines;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long el = t / lpe;
+    const int lam = (int)(t - el * lpe);
+    int e[3];
+    e[0] = (int)(el % g.n[0]);
+    const long long rest = el / g.n[0];
+    e[1] = (int)(rest % g.n[1]);
+    e[2] = (int)(rest / g.n[1]);
+    if (dim == 2) e[2] = 0;
+    // the other local indices of the line, in increasing direction order
+    int l0[3] = {0, 0, 0};
+    {
+      int r = lam;
+      for (int d2 = 0; d2 < dim; ++d2) {
+        if (d2 == d) continue;
+        l0[d2] = r % n1;
+        r /= n1;
+      }
+    }
+    const int lb = local_of(g, l0), st = lstride(g, d);
     const long long ec = elem_of(g, e);
-    double Lc[3] = {0.0, 0.0, 0.0};
-    for (int d = 0; d < dim; ++d) {
-      const long long em = elem_shift(g, e, d, -1), ep = elem_shift(g, e, d, +1);
-      const int m = l[d];
-      int l0[3] = {l[0], l[1], l[2]};
-      l0[d] = 0;
-      const int lb = local_of(g, l0), st = lstride(g, d);
-      const double* Vd = p.V[d];
-      // normal velocity traces at the faces e-1/2 and e+1/2
-      const double vd_l_m = trace(Vd, em, g.npe, lb, st, n1, phi1);  // from e-1
-      const double vd_l_p = trace(Vd, ec, g.npe, lb, st, n1, phi0);  // from e
-      const double vd_r_m = trace(Vd, ec, g.npe, lb, st, n1, phi1);  // from e
-      const double vd_r_p = trace(Vd, ep, g.npe, lb, st, n1, phi0);  // from e+1
-      const double s_l = 2.0 * fmax(fabs(vd_l_m), fabs(vd_l_p));
-      const double s_r = 2.0 * fmax(fabs(vd_r_m), fabs(vd_r_p));
-      const double* vdc = Vd + ec * g.npe + lb;
-      for (int c = 0; c < dim; ++c) {
-        const double* Q = p.V[c];
-        const double q_l_m = trace(Q, em, g.npe, lb, st, n1, phi1);
-        const double q_l_p = trace(Q, ec, g.npe, lb, st, n1, phi0);
-        const double q_r_m = trace(Q, ec, g.npe, lb, st, n1, phi1);
-        const double q_r_p = trace(Q, ep, g.npe, lb, st, n1, phi0);
-        const double f_l = 0.5 * (q_l_m * vd_l_m + q_l_p * vd_l_p) - 0.5 * s_l * (q_l_p - q_l_m);
-        const double f_r = 0.5 * (q_r_m * vd_r_m + q_r_p * vd_r_p) - 0.5 * s_r * (q_r_p - q_r_m);
-        const double* qc = Q + ec * g.npe + lb;
+    const long long em = elem_shift(g, e, d, -1), ep = elem_shift(g, e, d, +1);
+    const double* Vd = p.V[d];
+    const double vd_l_m = trace(Vd, em, g.npe, lb, st, n1, phi1);
+    const double vd_l_p = trace(Vd, ec, g.npe, lb, st, n1, phi0);
+    const double vd_r_m = trace(Vd, ec, g.npe, lb, st, n1, phi1);
+    const double vd_r_p = trace(Vd, ep, g.npe, lb, st, n1, phi0);
+    const double s_l = 2.0 * fmax(fabs(vd_l_m), fabs(vd_l_p));
+    const double s_r = 2.0 * fmax(fabs(vd_r_m), fabs(vd_r_p));
+    const double* vdc = Vd + ec * g.npe + lb;
+    for (int c = 0; c < dim; ++c) {
+      const double* Q = p.V[c];
+      const double q_l_m = trace(Q, em, g.npe, lb, st, n1, phi1);
+      const double q_l_p = trace(Q, ec, g.npe, lb, st, n1, phi0);
+      const double q_r_m = trace(Q, ec, g.npe, lb, st, n1, phi1);
+      const double q_r_p = trace(Q, ep, g.npe, lb, st, n1, phi0);
+      const double f_l = 0.5 * (q_l_m * vd_l_m + q_l_p * vd_l_p) - 0.5 * s_l * (q_l_p - q_l_m);
+      const double f_r = 0.5 * (q_r_m * vd_r_m + q_r_p * vd_r_p) - 0.5 * s_r * (q_r_p - q_r_m);
+      const double* qc = Q + ec * g.npe + lb;
+      for (int m = 0; m < n1; ++m) {
         double vol = 0.0;
         for (int k = 0; k < n1; ++k) vol += w[k] * Dn[k * n1 + m] * qc[k * st] * vdc[k * st];
         const double surf = phi1[m] * f_r - phi0[m] * f_l;
-        Lc[c] -= p.invdx[d] * winv[m] * (surf - vol);
+        const long long idx = ec * g.npe + lb + (long long)m * st;
+        const double Lv = (p.first ? 0.0 : p.L[c][idx]) - p.invdx * winv[m] * (surf - vol);
+        if (p.last) {
+          const double v0 = p.a != 0.0 ? p.V0[c][idx] : 0.0;
+          p.out[c][idx] = p.a * v0 + p.b * (Q[idx] + p.dt * Lv);
+        } else {
+          p.L[c][idx] = Lv;
+        }
       }
-    }
-    for (int c = 0; c < dim; ++c) {
-      const double v = p.V[c][idx];
-      const double v0 = p.a != 0.0 ? p.V0[c][idx] : 0.0;
-      p.out[c][idx] = p.a * v0 + p.b * (v + p.dt * Lc[c]);
     }
   }
 }
+
 
 __global__ void __launch_bounds__(kThreads)
     k_mass(Geo g, const double* __restrict__ F, double* __restrict__ b, double* __restrict__ x0,
@@ -761,19 +783,29 @@ cudaError_t k_main_to_dual(const sdg_handle* h, int d, const double* in, double*
 }
 cudaError_t k_convect_stage(const sdg_handle* h, const double* const* V0, const double* const* V,
                             double* const* out, double a, double b, double dt, cudaStream_t s) {
-  ConvectParams p;
-  p.g = h->g;
-  for (int d = 0; d < 3; ++d) {
-    p.invdx[d] = d < h->dim ? 1.0 / h->dx[d] : 0.0;
-    p.V0[d] = d < h->dim && V0 ? V0[d] : nullptr;
-    p.V[d] = d < h->dim ? V[d] : nullptr;
-    p.out[d] = d < h->dim ? out[d] : nullptr;
+  const long long nlines = h->g.ndof / h->g.n1;
+  for (int d = 0; d < h->dim; ++d) {
+    ConvLineParams q;
+    q.g = h->g;
+    q.d = d;
+    q.first = d == 0;
+    q.last = d == h->dim - 1;
+    q.invdx = 1.0 / h->dx[d];
+    for (int c = 0; c < 3; ++c) {
+      const bool on = c < h->dim;
+      q.V0[c] = on && V0 ? V0[c] : nullptr;
+      q.V[c] = on ? V[c] : nullptr;
+      q.L[c] = on ? h->Lc[c] : nullptr;
+      q.out[c] = on ? out[c] : nullptr;
+    }
+    q.a = a;
+    q.b = b;
+    q.dt = dt;
+    k_convect_line<<<grid_full(nlines), kThreads, 0, s>>>(q, h->mats);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
-  p.a = a;
-  p.b = b;
-  p.dt = dt;
-  k_convect<<<grid_full(h->g.ndof), kThreads, 0, s>>>(p, h->mats);
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 cudaError_t k_mass_rhs(const sdg_handle* h, const double* F, double* b, double* x0, cudaStream_t s) {
   k_mass<<<grid_full(h->g.ndof), kThreads, 0, s>>>(h->g, F, b, x0, h->mats);
