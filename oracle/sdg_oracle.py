@@ -514,7 +514,7 @@ class Oracle:
             vec.append(V)
         return np.array(lam), np.array(vec)  # (n, n1), (n, n1, n1)
 
-    def block_circulant_solve(self, b, x0, cmass, scale, raw=False):
+    def block_circulant_solve(self, b, x0, cmass, scale, raw=False, refine=2):
         """Exact solution of (cmass M^{xyz} + scale * A') x = b on the periodic
         grid, A' = dt sum_d (1/dx_d^2) M^{perp d} H_d (Eq. pSyst).  The operator
         is block-circulant: a discrete Fourier transform over the elements of
@@ -525,7 +525,27 @@ class Oracle:
         diagonalise.  Zero eigenvalues (the kernel, cmass = 0) are dropped and
         the kernel part of x0 is kept, as CG from x0 does (raw: the spectral
         solution itself, W-orthogonal to the kernel, is returned; this map is
-        symmetric, the projected one is not)."""
+        symmetric, the projected one is not).
+
+        The Fourier solve alone carries the rounding of its transforms into
+        every mode, which the ill-conditioned pressure system turns into a
+        relative solution error of about 4e-11 on 128^2 cells at N = 7; each
+        of the `refine` residual corrections x += S (b - A x), with S the
+        spectral inverse and A the operator applied term by term, brings the
+        solution to the accuracy FP64 can represent (its residual then equals
+        the residual that rounding the exact solution to FP64 leaves)."""
+        def op(X):
+            Y = scale * self.Aprime(X)
+            return Y + cmass * self.mass_all(X) if cmass != 0.0 else Y
+        x = self._spectral_inverse(b, cmass, scale)
+        for _ in range(refine):
+            x = x + self._spectral_inverse(b - op(x), cmass, scale)
+        if cmass == 0.0 and not raw:
+            x = x - self.kernel_part(x) + self.kernel_part(x0)
+        return x
+
+    def _spectral_inverse(self, b, cmass, scale):
+        """One Fourier-space solve of block_circulant_solve (kernel dropped)."""
         dim = self.dim
         eax = [self._eax(d) for d in range(dim)]
         lax = [self._lax(d) for d in range(dim)]
@@ -565,10 +585,7 @@ class Oracle:
             shp = [1] * (2 * dim)
             shp[lax[d]] = self.n1
             Y = Y / sq.reshape(shp)
-        x = np.real(np.fft.ifftn(Y, axes=eax))
-        if cmass == 0.0 and not raw:
-            x = x - self.kernel_part(x) + self.kernel_part(x0)
-        return x
+        return np.real(np.fft.ifftn(Y, axes=eax))
 
     def pressure_solve_exact(self, b, x0):
         """theta A' x = b solved exactly (block_circulant_solve)."""

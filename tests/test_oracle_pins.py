@@ -567,6 +567,36 @@ def test_block_circulant_solve_matches_dense(dim, n, N):
     assert np.linalg.norm(xv - np.linalg.solve(Av, bv)) <= 1e-12 * np.linalg.norm(xv)
 
 
+def test_exact_solve_reaches_fp64_floor():
+    """Eq. pSyst on 32x32 cells at N = 7 (the benchmark degree): for a range
+    right-hand side b = theta A' z the exact solve returns the range part of z
+    to 3e-13 (the rounding of b itself costs about 1e-13 here), and its
+    residual equals, within 1.5x, the residual that rounding the exact
+    solution to FP64 leaves by itself: theta A' applied to a random
+    perturbation of +-ulp(x)/(2 sqrt 3) per entry (the root mean square of a
+    rounding error).  Without its residual corrections the Fourier solve
+    leaves more than 4x that residual (and the gap grows with the grid)."""
+    o = _oracle(2, (32, 32), 7, nu=1e-3, theta=0.51, dt=2e-3, L=(2 * math.pi, 2 * math.pi))
+    X, Y = o.coords(None)
+    z = np.cos(X) * np.cos(2 * Y) + 0.3 * np.sin(3 * X + 1.0) * np.cos(5 * Y)
+    z = z - o.kernel_part(z)
+    b = o.pressure_apply(z)
+    b = b - o.kernel_part(b)
+    nb = np.linalg.norm(b)
+    s = np.random.default_rng(5).choice([-1.0, 1.0], size=b.shape)
+    for refine, ok in ((2, True), (0, False)):
+        x = o.block_circulant_solve(b, np.zeros_like(b), 0.0, o.theta, refine=refine)
+        fwd = np.linalg.norm(x - z) / np.linalg.norm(z)
+        r = b - o.pressure_apply(x)
+        res = np.linalg.norm(r - o.kernel_part(r)) / nb
+        floor = np.linalg.norm(o.pressure_apply(0.5 * np.spacing(np.abs(x)) * s / math.sqrt(3.0))) / nb
+        if ok:
+            assert fwd <= 3e-13, fwd
+            assert res <= 1.5 * floor, (res, floor)
+        else:
+            assert res > 4 * floor, (fwd, res, floor)
+
+
 def test_exact_step_matches_cg_step():
     """step_exact (both systems solved exactly) equals step with CG run to
     1e-14 on a small grid."""
