@@ -522,22 +522,45 @@ def test_tg_kinetic_energy_decay():
     assert abs(K - rows[1][2]) / rows[1][2] < 1e-3
 
 
-@pytest.mark.parametrize("N", [2, 3])
-def test_step_spatial_order(N):
-    """Inviscid Taylor-Green is a steady Euler solution; three small steps
-    (dt = 1e-3) keep it to a spatial error that converges at order >= N under
-    grid refinement.  (Every step projects dual -> main -> dual, Eqs.
-    l2forward / l2backward, each an O(h^{N+1}) perturbation.)"""
+def _l2_velocity_error(o, U, Ue):
+    """sqrt(int |u_h - u|^2) over the domain, GL quadrature on each dual grid."""
+    cv = float(np.prod(o.g.dx))
+    return math.sqrt(sum(cv * float(np.sum(o.mass_all((U[d] - Ue[d]) ** 2))) for d in range(o.dim)))
+
+
+@pytest.mark.parametrize("N,cells,min_order", [(2, (8, 16, 32), 2.5), (3, (4, 8, 16), 2.75),
+                                               (4, (8, 16, 32), 4.5), (5, (4, 8), 5.5)])
+def test_step_convergence_order(N, cells, min_order):
+    """Spatial convergence of the whole step on the viscous 2D Taylor-Green
+    vortex (exact solution of Sec. 3.4.2): nu = 0.05, theta = 0.5, L2 velocity
+    error at T = 0.02 on refined grids.  The fractional step is first order in
+    dt (Sec. 2.3); Richardson extrapolation 2 U(dt/2) - U(dt) with dt = 1e-3
+    removes that error, so what remains is the spatial one.
+
+    Even N and N = 5 converge at order N + 1 (measured: N = 2: 3.2, 3.7;
+    N = 4: 4.8, 5.8; N = 5: 6.0), asserted >= N + 1/2.  N = 3 converges at
+    order N (measured 3.2, 3.0): already the discrete divergence-free
+    projection of the interpolated initial field moves it by O(h^N) for this
+    degree, while the round trip of the L2 projections of Eqs.
+    l2forward / l2backward alone is O(h^{N+1}).  The paper's own Taylor-Green
+    convergence table (Table TGV2D, space-time version of the same spatial
+    scheme) shows the same pattern: 3.26-3.28 for N = M = 3 against 3.6-3.9
+    for N = M = 2 and 5.9-6.3 for N = M = 4.  A dropped order fails every
+    case."""
     errs = []
-    for n in (4, 8, 16):
-        o = _oracle(2, (n, n), N, nu=0.0, theta=0.5, dt=1e-3)
-        Us, P = _tg_state(o)
-        U0 = [U.copy() for U in Us]
-        for _ in range(3):
-            Us, P, _ = o.step(Us, P)
-        errs.append(max(np.abs(Us[c] - U0[c]).max() for c in range(2)))
-    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
-    assert min(orders) >= N - 0.25, orders
+    T = 0.02
+    for n in cells:
+        sols = []
+        for dt in (1e-3, 5e-4):
+            o = _oracle(2, (n, n), N, nu=0.05, theta=0.5, dt=dt)
+            Us, P = _tg_state(o)
+            for _ in range(int(round(T / dt))):
+                Us, P = o.step_exact(Us, P)
+            sols.append(Us)
+        Ue, _ = _tg_state(o, T)
+        errs.append(_l2_velocity_error(o, [2.0 * sols[1][d] - sols[0][d] for d in range(2)], Ue))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert min(orders) >= min_order, (errs, orders)
 
 
 # ------------------------------------------------------------------ exact periodic solves
