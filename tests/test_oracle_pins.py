@@ -620,6 +620,49 @@ def test_exact_solve_reaches_fp64_floor():
             assert res > 4 * floor, (fwd, res, floor)
 
 
+@pytest.mark.parametrize("N,odd", [(5, True), (4, False)])
+def test_pressure_sensitivity_to_operator_rounding(N, odd):
+    """How precisely FP64 fixes the pressure of a step: perturb the 1D blocks
+    H^R, H^L = (H^R)^T and H^C (after Eq. pSyst) by a random symmetric amount
+    of 1e-15 of their size (a few units in the last place, the size of the
+    rounding any FP64 evaluation of them carries) and step a perturbed
+    Taylor-Green field on 32x32 cells with both systems solved exactly.  The
+    velocity moves by < 1e-13.  For odd N the pressure moves by > 3e-12
+    (measured 1.1e-11 here, 2.2e-10 on 64x64 cells at N = 7): its
+    near-kernel modes, per-cell sawtooth patterns modulated by smooth
+    envelopes (the kernel of Sec. 2.1 is larger than the constants for odd
+    N), have small eigenvalues that such rounding shifts noticeably, and
+    they hardly enter the gradient that updates the velocity.  For even N
+    (kernel: the constants) it moves by < 1e-12 (measured 3.8e-13).  Two
+    independent FP64 implementations of the step therefore agree in velocity
+    to round-off but, for odd N on large grids, in pressure only to this
+    sensitivity."""
+    o = _oracle(2, (32, 32), N, nu=1e-3, theta=0.51, dt=2e-3, L=(2 * math.pi, 2 * math.pi))
+    modes = si.stream_modes(0, 32, 8, 1e-2)
+    Xu, Yu = o.coords(0)
+    Xv, Yv = o.coords(1)
+    X, Y = o.coords(None)
+    U = [si.taylor_green_2d(Xu, Yu)[0] + si.perturbation_velocity(modes, Xu, Yu)[0],
+         si.taylor_green_2d(Xv, Yv)[1] + si.perturbation_velocity(modes, Xv, Yv)[1]]
+    P = si.taylor_green_2d(X, Y)[2]
+    U1, P1 = o.step_exact([u.copy() for u in U], P.copy())
+    rng = np.random.default_rng(3)
+    E = rng.standard_normal(o.B.HR.shape) * 1e-15 * np.abs(o.B.HR).max()
+    C = rng.standard_normal(o.B.HC.shape) * 1e-15 * np.abs(o.B.HC).max()
+    o.B.HR = o.B.HR + E
+    o.B.HL = o.B.HL + E.T
+    o.B.HC = o.B.HC + 0.5 * (C + C.T)
+    U2, P2 = o.step_exact([u.copy() for u in U], P.copy())
+    du = math.sqrt(sum(float(np.sum((a - b) ** 2)) for a, b in zip(U1, U2)))
+    du /= math.sqrt(sum(float(np.sum(a * a)) for a in U1))
+    dp = np.linalg.norm(P1 - P2) / np.linalg.norm(P1)
+    assert du < 1e-13, du
+    if odd:
+        assert dp > 3e-12, dp
+    else:
+        assert dp < 1e-12, dp
+
+
 def test_exact_step_matches_cg_step():
     """step_exact (both systems solved exactly) equals step with CG run to
     1e-14 on a small grid."""
