@@ -8,8 +8,11 @@
 // its scratch (the per-block partial sums and the ticket counter of the
 // last-block reduction) is the file-scope array below, which every GPU that
 // loads the library holds until the process exits.
+#include <cuda.h>
+
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 
 #include "sdg_device.cuh"
 
@@ -27,9 +30,44 @@ constexpr long long kMaxDof = (long long)kMaxBlocks * kThreads * kPerThread;  //
 static __device__ __align__(256) double g_scratch[kMaxBlocks + 32];
 
 // Device address of g_scratch per device (host code may not use the symbol
-// itself as a device pointer).  Filled on the first call on each device.
+// itself as a device pointer), looked up on the first call in each CUDA
+// context of a device and keyed by that context's unique id, so that a
+// replaced context (after cudaDeviceReset, or another driver context made
+// current) triggers a fresh look-up instead of reusing a stale address.
 constexpr int kMaxDevices = 64;
-double* g_addr[kMaxDevices] = {nullptr};
+struct ScratchSlot {
+  unsigned long long ctx_id;
+  double* addr;
+};
+ScratchSlot g_slot[kMaxDevices] = {};
+std::mutex g_slot_mu;
+
+// Driver entry points for the current context's id (taken through the
+// runtime, so the library does not link the driver library itself).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+std::once_flag g_fn_once;
+
+bool current_context_id(unsigned long long* id) {
+  std::call_once(g_fn_once, [] {
+    void* f0 = nullptr;
+    void* f1 = nullptr;
+    cudaDriverEntryPointQueryResult q0, q1;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0) == cudaSuccess &&
+        q0 == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess) {
+      g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f0);
+      g_ctx_id = reinterpret_cast<CtxGetIdFn>(f1);
+    }
+  });
+  if (!g_ctx_current || !g_ctx_id) return false;
+  CUcontext ctx = nullptr;
+  if (g_ctx_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return false;
+  return g_ctx_id(ctx, id) == CUDA_SUCCESS;
+}
 
 struct KeParams {
   sdg::Geo g;
@@ -124,16 +162,34 @@ int sdg_kinetic_energy_noalloc(const sdg_grid* grid, int N, const double* u, con
     sdg::set_last_error("sdg_kinetic_energy_noalloc: no usable current device");
     return SDG_ERR_CUDA;
   }
-  if (g_addr[dev] == nullptr) {
-    // one-time set-up on this device (the device is current): the device
-    // address of the scratch array
-    double* ptr = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_scratch);
-    if (e != cudaSuccess || ptr == nullptr) {
-      sdg::set_last_error("sdg_kinetic_energy_noalloc: cudaGetSymbolAddress failed");
-      return SDG_ERR_CUDA;
+  // id of the current context (none yet if this thread has not used the
+  // runtime on this device: the symbol look-up below creates it)
+  unsigned long long ctx_id = 0;
+  const bool have_id = current_context_id(&ctx_id);
+  double* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_slot_mu);
+    ScratchSlot& slot = g_slot[dev];
+    if (!have_id || slot.addr == nullptr || slot.ctx_id != ctx_id) {
+      // set-up, once per context of this device (the device is current):
+      // the device address of the scratch array
+      double* ptr = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_scratch);
+      if (e != cudaSuccess || ptr == nullptr) {
+        char msg[200];
+        std::snprintf(msg, sizeof(msg), "sdg_kinetic_energy_noalloc: cudaGetSymbolAddress failed: %s",
+                      cudaGetErrorString(e));
+        sdg::set_last_error(msg);
+        return SDG_ERR_CUDA;
+      }
+      if (!have_id && !current_context_id(&ctx_id)) {
+        sdg::set_last_error("sdg_kinetic_energy_noalloc: cannot identify the current CUDA context");
+        return SDG_ERR_CUDA;
+      }
+      slot.addr = ptr;
+      slot.ctx_id = ctx_id;
     }
-    g_addr[dev] = ptr;
+    scratch = slot.addr;
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   KeParams p{};
@@ -145,13 +201,22 @@ int sdg_kinetic_energy_noalloc(const sdg_grid* grid, int N, const double* u, con
   sdg::gauss_legendre(g.n1, xi, p.w);
   p.scale = 0.5 * cellvol / vol;
   p.out = ke;
-  p.scratch = g_addr[dev];
+  p.scratch = scratch;
   long long blocks = (g.ndof + (long long)kThreads * kPerThread - 1) / ((long long)kThreads * kPerThread);
   if (blocks < 1) blocks = 1;
   // the ticket counter must start at zero (the last block also resets it)
-  if (cudaMemsetAsync(p.scratch + kMaxBlocks, 0, sizeof(unsigned int), s) != cudaSuccess) return SDG_ERR_CUDA;
-  k_ke_noalloc<<<(unsigned)blocks, kThreads, 0, s>>>(p);
-  return cudaGetLastError() == cudaSuccess ? SDG_OK : SDG_ERR_CUDA;
+  cudaError_t e = cudaMemsetAsync(p.scratch + kMaxBlocks, 0, sizeof(unsigned int), s);
+  if (e == cudaSuccess) {
+    k_ke_noalloc<<<(unsigned)blocks, kThreads, 0, s>>>(p);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    char msg[200];
+    std::snprintf(msg, sizeof(msg), "sdg_kinetic_energy_noalloc: CUDA error %s", cudaGetErrorString(e));
+    sdg::set_last_error(msg);
+    return SDG_ERR_CUDA;
+  }
+  return SDG_OK;
 }
 
 }  // extern "C"
