@@ -51,8 +51,9 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed plain-FP64 steps (after one warm-up)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--tg3d-steps", type=int, default=1,
-                    help="timed steps of the 3D 48^3, N = 4 workload (after one warm-up); 0 skips it")
+    ap.add_argument("--tg3d-steps", type=int, default=20,
+                    help="timed steps of the 3D 48^3, N = 4 workload in each precision (after one warm-up); "
+                         "0 skips it")
     ap.add_argument("--batch-steps", type=int, default=1,
                     help="timed steps of the 48-problem batch (after one warm-up); 0 skips it")
     return ap.parse_args()
@@ -121,15 +122,15 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def ncu_traffic():
-    """DRAM bytes per launch of the fused FP32 operator from a committed ncu
-    summary (null when absent)."""
+def ncu_traffic(workload=WORKLOAD):
+    """DRAM bytes per launch of the fused FP32 operator on `workload` from a
+    committed ncu summary (null when absent)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    return d.get(WORKLOAD, {}).get("fused_apply_f32_bytes")
+    return d.get(workload, {}).get("fused_apply_f32_bytes")
 
 
 def reduce_over_ranks(dist, step_ms, solve_ms, work, device):
@@ -181,28 +182,74 @@ def oracle_sample_pressure_solve(cells=CPU_SAMPLE_CELLS):
     return o.ndof * applies / dt / 1e9, dt, o.ndof, applies
 
 
+def _oracle_worker(cells):
+    """One oracle sample solve in a pool process: (DOF x applications, seconds)."""
+    _, secs, dof, applies = oracle_sample_pressure_solve(tuple(cells))
+    return dof * applies, secs
+
+
+def host_cpu():
+    """(logical cores, CPU model name) of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return os.cpu_count() or 1, model
+
+
+def oracle_all_cores(cells, rounds=1, procs=None):
+    """The oracle on every host core: `procs` single-threaded processes (spawn
+    start method) each solve the same sample, `rounds` times; throughput =
+    all their work / wall time.  Returns (GDOF/s, wall seconds per round,
+    processes, DOF x applications per round)."""
+    import multiprocessing as mp
+    procs = procs or (os.cpu_count() or 1)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        pool.map(_oracle_worker, [(4, 4)] * procs)  # imports and first calls, untimed
+        work, t0 = 0.0, time.perf_counter()
+        for _ in range(rounds):
+            work += sum(w for w, _ in pool.map(_oracle_worker, [cells] * procs))
+        wall = time.perf_counter() - t0
+    return work / wall / 1e9, wall / rounds, procs, work / rounds
+
+
 # ----------------------------------------------------------------- reference arm
+REF_SAMPLE_CELLS = (24, 24)      # reference arm: one pool round per step, ~5 s
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    # warm-up: tiny oracle solves (numpy has no compile step)
-    for _ in range(args.warmup):
-        oracle_sample_pressure_solve((4, 4))
-    vals, secs = [], []
-    dof = applies = 0
-    for _ in range(args.steps):
-        v, s, dof, applies = oracle_sample_pressure_solve()
-        vals.append(v)
-        secs.append(s)
-    value = sum(dof * applies for _ in vals) / sum(secs) / 1e9
-    sample = (f"oracle pressure CG (numpy FP64, rtol 1e-12) on {CPU_SAMPLE_CELLS[0]}x{CPU_SAMPLE_CELLS[1]} "
-              f"cells of the {WORKLOAD} workload ({dof} DOF, {applies} operator applications)")
+    cores, model = host_cpu()
+    # warm-up: tiny oracle solves in the pool (numpy has no compile step)
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    secs, work = [], 0.0
+    with ctx.Pool(cores) as pool:
+        for _ in range(args.warmup):
+            pool.map(_oracle_worker, [(4, 4)] * cores)
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            work += sum(w for w, _ in pool.map(_oracle_worker, [REF_SAMPLE_CELLS] * cores))
+            secs.append(time.perf_counter() - t0)
+    value = work / sum(secs) / 1e9
+    n1 = 8
+    dof = REF_SAMPLE_CELLS[0] * REF_SAMPLE_CELLS[1] * n1 * n1
+    sample = (f"oracle pressure CG (numpy FP64, rtol 1e-12) on {REF_SAMPLE_CELLS[0]}x{REF_SAMPLE_CELLS[1]} "
+              f"cells of the {WORKLOAD} workload ({dof} DOF), one single-threaded solve per host core per "
+              f"step ({cores} processes, spawn pool; CPU: {model})")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_cells": list(CPU_SAMPLE_CELLS)},
-            "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_cells": list(REF_SAMPLE_CELLS)},
+            "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -256,6 +303,7 @@ def run_ours(args):
     p_applies = 0
     launches = 0
     p_iters = []
+    p_true, p_floor = [], []
     for k in range(args.steps):
         flush.fill_(float(k))  # evict L2 between steps (outside the step's events)
         ev[k][0].record(stream)
@@ -266,6 +314,8 @@ def run_ours(args):
         p_applies += info["pressure_applies"]
         launches += info["kernel_launches"]
         p_iters.append(info["pressure"]["iters"])
+        p_true.append(info["pressure"]["true_res"])
+        p_floor.append(info["pressure"]["floor_res"])
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
@@ -339,23 +389,30 @@ def run_ours(args):
             f_pms += info["pressure_ms"]
             f_app += info["pressure_applies"]
             f_it.append(info["pressure"]["iters"])
+            f_true = info["pressure"]["true_res"]
+            f_floor = info["pressure"]["floor_res"]
             if k == 0:
                 U64 = [torch.empty_like(Us[0]) for _ in range(2)]
                 P64 = torch.empty_like(Us[0])
                 h.get_state(U64, P64)
         fp64 = {"gdofs": ndof * f_app / (f_pms * 1e-3) / 1e9, "ms_per_step": statistics.mean(f_ms),
-                "pressure_iters": f_it, "steps": args.fp64_steps, "warmup": 1}
+                "pressure_iters": f_it, "steps": args.fp64_steps, "warmup": 1,
+                "pressure_true_res": f_true, "pressure_floor_res": f_floor}
         # the same step in mixed precision from state S
         h.set_options(sdg.SDG_MIXED, 1e-12, 1e-12)
         h.set_state(S[0], S[1])
-        h.step(1)
+        m_info = h.step(1)
         Um = [torch.empty_like(Us[0]) for _ in range(2)]
         Pm = torch.empty_like(Us[0])
         h.get_state(Um, Pm)
         relerr = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
         accuracy = {"mixed_vs_fp64_rel_l2": {"u": relerr(Um[0], U64[0]), "v": relerr(Um[1], U64[1]),
                                              "p": relerr(Pm, P64)},
-                    "speedup_mixed_over_fp64_step": statistics.mean(f_ms) / (tot_step_ms / args.steps)}
+                    "pressure_true_res": {"mixed": m_info["pressure"]["true_res"], "fp64": f_true},
+                    "pressure_floor_res": m_info["pressure"]["floor_res"],
+                    "speedup_mixed_over_fp64_step": statistics.mean(f_ms) / (tot_step_ms / args.steps),
+                    "note": ("both solves stop on the true FP64 residual <= max(rtol, 3 floor_res), floor_res "
+                             "the residual that rounding the solution to FP64 leaves")}
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -378,36 +435,64 @@ def run_ours(args):
                "h2d_bytes_per_step": 3 * ndof * 8, "d2h_bytes_per_step": 3 * ndof * 8,
                "ms_per_step": 1000 * t_tot / args.e2e_steps}
 
-    # ---- 3D workload: 48^3 cells, N = 4 (block hepta-diagonal pressure system)
+    # ---- 3D workload: 48^3 cells, N = 4 (block hepta-diagonal pressure system):
+    # the same steps from the same state in mixed precision and in FP64,
+    # kinetic energy after every step, and the roofline of the 3D operator
     tg3d = None
     if args.tg3d_steps > 0:
         w3, U3, P3 = workload_state("tg3d_48_N4")
         h3 = sdg.Handle(3, w3["n"], w3["L"], w3["N"], w3["nu"], w3["theta"], w3["dt"])
         h3.set_convection_substeps(w3["nsub"])
-        res3 = {}
+        res3, K3 = {}, {}
         for prec, name in ((sdg.SDG_MIXED, "mixed"), (sdg.SDG_FP64, "fp64")):
             h3.set_options(prec, 1e-12, 1e-12)
             h3.set_state([dev(u) for u in U3], dev(P3))
             assert h3.step(1)["status"] == sdg.SDG_OK  # warm-up
-            flush.fill_(0.25)
-            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            a.record(stream)
-            pms, app, its = 0.0, 0, []
-            for _ in range(args.tg3d_steps):
+            h3.set_state([dev(u) for u in U3], dev(P3))
+            ms, pms, app, its, ks, trs, launches3 = 0.0, 0.0, 0, [], [], [], 0
+            for k in range(args.tg3d_steps):
+                flush.fill_(0.25 + k)
+                a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
                 inf = h3.step(1)
+                e.record(stream)
+                torch.cuda.synchronize()
                 assert inf["status"] == sdg.SDG_OK, inf
+                ms += a.elapsed_time(e)
                 pms += inf["pressure_ms"]
                 app += inf["pressure_applies"]
+                launches3 += inf["kernel_launches"]
                 its.append(inf["pressure"]["iters"])
-            e.record(stream)
-            torch.cuda.synchronize()
-            ke, _ = h3.diagnostics()
-            res3[name] = {"ms_per_step": a.elapsed_time(e) / args.tg3d_steps,
+                trs.append(inf["pressure"]["true_res"])
+                ks.append(h3.diagnostics()[0])  # outside the step's events
+            K3[name] = ks
+            res3[name] = {"ms_per_step": ms / args.tg3d_steps,
                           "pressure_gdofs": h3.ndof * app / (pms * 1e-3) / 1e9, "pressure_iters": its,
-                          "kinetic_energy_after": ke}
+                          "pressure_true_res_max": max(trs), "kinetic_energy": [ks[0], ks[-1]],
+                          "gpu_launches": launches3}
+        # roofline of the fused FP32 3D operator: one more mixed step with events
+        # around each of its launches
+        h3.set_options(sdg.SDG_MIXED, 1e-12, 1e-12)
+        h3.set_profiling(True)
+        flush.fill_(-2.0)
+        assert h3.step(1)["status"] == sdg.SDG_OK
+        c3 = h3.counters()
+        h3.set_profiling(False)
+        n3 = c3["apply_launches"][1]
+        avg3 = c3["apply_ms"][1] / n3 if n3 else float("nan")
+        b3 = BYTES_PER_DOF_FUSED_F32 * h3.ndof
+        ach3 = b3 / (avg3 * 1e-3) / 1e9
+        hbm_peak3 = float(measured_peaks()[0].get("hbm_gbs", 6800.0))
+        dK = max(abs(a - b) / abs(b) for a, b in zip(K3["mixed"], K3["fp64"]))
         tg3d = {"workload": "tg3d_48_N4 (3D TG, 48^3 cells, N 4, nu 1/1600, dt 1e-3, rtol 1e-12)",
-                "dof": h3.ndof, "steps": args.tg3d_steps, "warmup": 1, **res3}
+                "dof": h3.ndof, "steps": args.tg3d_steps, "warmup": 1, **res3,
+                "kinetic_energy_mixed_vs_fp64_max_rel": dK,
+                "roofline": {"bound": "hbm", "achieved": ach3, "peak": hbm_peak3, "unit": "GB/s",
+                             "frac": ach3 / hbm_peak3, "traffic": ncu_traffic("tg3d_48_N4"),
+                             "kernel": "k_apply3m<float,5> (fused z-marching CG operator; events around each launch "
+                                       "in one extra mixed step)",
+                             "avg_launch_us": avg3 * 1e3, "launches_timed": n3,
+                             "algorithmic_bytes_per_launch": b3}}
         h3.close()
 
     # ---- batched workload: 48 independent problems stepped concurrently
@@ -421,34 +506,42 @@ def run_ours(args):
             m.set_options(sdg.SDG_MIXED, 1e-12, 1e-12)
             m.set_convection_substeps(bw["nsub"][i])
             m.set_state([dev(u) for u in U], dev(P))
-        rc, _ = bt.step(1)  # warm-up
-        assert rc == sdg.SDG_OK
+        okc = (sdg.SDG_OK, sdg.SDG_ERR_NOT_CONVERGED)
+        rc, _ = bt.step(1, ok=okc)  # warm-up
         flush.fill_(0.5)
         a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         a.record(stream)
-        rc, infos = bt.step(args.batch_steps, stream=stream)
+        rc, infos = bt.step(args.batch_steps, stream=stream, ok=okc)
         e.record(stream)
         torch.cuda.synchronize()
-        assert rc == sdg.SDG_OK
         ms = a.elapsed_time(e)
         work = sum(m.ndof * inf["pressure_applies"] for m, inf in zip(bt.members, infos))
+        short = [(i, bt.members[i].N, inf["pressure"]["true_res"]) for i, inf in enumerate(infos)
+                 if inf["pressure"]["status"] != sdg.SDG_OK]
         batch = {"workload": "batch48_seed2 (2D, 16^2..128^2 cells, N 2..11, mixed, rtol 1e-12)",
                  "problems": len(bt), "dof_total": sum(m.ndof for m in bt.members),
                  "steps": args.batch_steps, "warmup": 1, "ms_per_step": ms / args.batch_steps,
                  "pressure_gdof_applies_per_s": work / (ms * 1e-3) / 1e9,
                  "pressure_iters_max": max(inf["pressure"]["iters"] for inf in infos),
+                 "pressure_true_res_max": max(inf["pressure"]["true_res"] for inf in infos),
+                 "members_short_of_rtol": [{"member": i, "N": N, "true_res": r} for i, N, r in short],
                  "threads": "min(48, 16, cores) host threads, one stream per member"}
         bt.close()
 
-    # ---- CPU baseline (rank 0, N = 1)
+    # ---- CPU baseline (rank 0, N = 1): the oracle on one core and on all of them
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, s, dof, applies = oracle_sample_pressure_solve()
-        cpu = {"value": v, "unit": "GDOF/s", "cores": 1, "kind": "oracle",
-               "sample": (f"oracle pressure CG (numpy FP64, rtol 1e-12, single thread) on "
-                          f"{CPU_SAMPLE_CELLS[0]}x{CPU_SAMPLE_CELLS[1]} cells of the workload: {dof} DOF, "
-                          f"{applies} operator applications, {s:.1f} s")}
+        v1, s1, dof, applies = oracle_sample_pressure_solve()
+        vall, wall, procs, _ = oracle_all_cores(CPU_SAMPLE_CELLS)
+        cores, model = host_cpu()
+        cpu = {"value": vall, "unit": "GDOF/s", "cores": procs, "kind": "oracle",
+               "single_core": {"value": v1, "cores": 1, "seconds": s1},
+               "cpu_model": model,
+               "sample": (f"oracle pressure CG (numpy FP64, rtol 1e-12) on {CPU_SAMPLE_CELLS[0]}x"
+                          f"{CPU_SAMPLE_CELLS[1]} cells of the workload: {dof} DOF, {applies} operator "
+                          f"applications; value: {procs} single-threaded processes (one per host core, spawn "
+                          f"pool) solving it at once, {wall:.1f} s wall; single_core: one process, {s1:.1f} s")}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
@@ -461,6 +554,7 @@ def run_ours(args):
                            "l2": "512 MB buffer written between timed steps (outside the step events)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "pressure_iters_per_step": p_iters, "pressure_ms_total": p_ms,
+                "pressure_true_res_max": max(p_true), "pressure_floor_res": max(p_floor),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "fp64": fp64, "accuracy": accuracy, "tg3d": tg3d, "batch": batch}
         print(json.dumps(line), flush=True)

@@ -39,10 +39,10 @@ typedef enum {
   SDG_OK = 0,
   SDG_ERR_INVALID_ARG = 1,   /* bad size, degree, parameter or NULL pointer */
   SDG_ERR_CUDA = 2,          /* a CUDA runtime call failed */
-  SDG_ERR_NOT_CONVERGED = 3, /* CG hit maxit; x holds the last iterate */
+  SDG_ERR_NOT_CONVERGED = 3, /* CG hit maxit or its true residual stopped improving
+                                above the tolerance; x holds the last iterate */
   SDG_ERR_BREAKDOWN = 4,     /* p^T A p <= 0 or not finite */
-  SDG_ERR_UNSUPPORTED = 5,   /* a configuration this build does not handle */
-  SDG_ERR_TIMEOUT = 6        /* reserved: a bounded device wait ran out */
+  SDG_ERR_UNSUPPORTED = 5    /* a configuration this build does not handle */
 } sdg_status;
 
 typedef enum { SDG_FP64 = 0, SDG_MIXED = 1 } sdg_precision;
@@ -54,13 +54,29 @@ typedef struct {
 } sdg_grid;
 
 typedef struct {
-  int iters;          /* CG iterations (mixed: FP32 iterations) */
+  int iters;          /* CG iterations (mixed: FP32 iterations; FP64
+                         iterations of a finishing phase count in
+                         applies_fp64) */
   int outer_iters;    /* mixed: FP64 residual replacements (0 in FP64) */
   int applies_fp64;   /* operator applications in FP64 */
   int applies_fp32;   /* operator applications in FP32 */
   double rel_res;     /* ||r|| / ||b||: recursive residual (FP64 mode) or
                          true FP64 residual (mixed mode) at exit */
   int status;         /* sdg_status of this solve */
+  double true_res;    /* ||b - A x|| / ||b|| of the returned x, recomputed in
+                         FP64 with the accurate operator (both modes; for the
+                         singular pressure system the constant part of the
+                         residual, round-off of a zero-mean b, is removed) */
+  double floor_res;   /* estimate of the smallest true_res any FP64 vector
+                         near x can have: ||A u|| / ||b|| for a perturbation
+                         u of random sign and size ulp(x_i) / (2 sqrt 3) per
+                         entry, the spread of rounding x to FP64 (0 when not
+                         computed: FP64 mode without info, mixed mode that
+                         met the tolerance) */
+  double eval_res;    /* ||A x - A~ x|| / ||b||: two FP64 evaluations of the
+                         operator at the returned x (accurate and direct
+                         contraction), the size of the rounding of A x itself;
+                         computed only when a solve stops improving (else 0) */
 } sdg_cg_info;
 
 typedef struct {
@@ -106,8 +122,10 @@ int sdg_kernel_projector(int N, double* proj, int* dim);
  * the local kernel (see sdg_kernel_projector).  Three host arrays of
  * (N+1)^2 doubles, row-major.  By construction HL = HR^T and Mc = Mc^T
  * (exactly, up to the extended-precision evaluation) and
- * (HL + Mc + HR) c = 0 for every kernel pattern c.  The plain FP64 CG
- * applies HL, H^C-part of Mc without correction, and HR.
+ * (HL + Mc + HR) c = 0 for every kernel pattern c.  Every CG iteration
+ * and true residual uses this form; the FP64 sdg_pressure_apply /
+ * sdg_viscous_apply and the pressure right-hand side apply HL, H^C and HR
+ * directly (the same operator in exact arithmetic).
  * Errors: INVALID_ARG. */
 int sdg_line_operator(int N, int fp32, double* HL, double* Mc, double* HR);
 
@@ -121,19 +139,42 @@ int sdg_create(const sdg_grid* grid, int N, double nu, double theta, double dt,
 int sdg_destroy(sdg_handle* h);
 
 /* Precision mode and CG controls: relative tolerances on ||r||/||b|| for the
- * pressure and viscous solves, cap on CG iterations per solve.
- *   SDG_FP64:  plain CG in FP64; stops on the recursive residual.
- *   SDG_MIXED: CG iterations and operator applications in FP32 with FP64
- *              reduction of every dot product; the correction is folded into
- *              the FP64 solution and the true residual b - A x is recomputed
- *              in FP64 ("reliable update") whenever the FP32 residual has
- *              dropped by the factor delta since the last update (or after
- *              max(2000, iterations/8) FP32 iterations); stops when the true
- *              FP64 residual meets the tolerance, or, once it no longer
- *              improves 2x over two updates (its FP64 round-off floor,
- *              about eps64 ||A|| ||x||), reports OK if it is within 10 rtol.
- *              (Plain FP64 CG stops on its recursive residual, whose true
- *              counterpart can be far larger on ill-conditioned systems.)
+ * pressure and viscous solves, cap on CG iterations per solve.  Both modes
+ * run the CG of Sec. 2.1 (no preconditioner) with the accurate operator (the
+ * contraction that removes the local kernel patterns first and annihilates
+ * them exactly, see sdg_line_operator), and both stop on the TRUE residual
+ * ||b - A x|| recomputed in FP64 ("residual replacement": the recomputed
+ * residual replaces the recursive one and the iteration continues in the
+ * same direction).
+ *   SDG_FP64:  iterations in FP64; the residual is replaced when the
+ *              recursion reports the tolerance (a long FP64 recursion drifts:
+ *              on 256 x 256 cells at N = 7 it reports 1e-12 when the true
+ *              residual is 7e-10).
+ *   SDG_MIXED: iterations and operator applications in FP32; the dot
+ *              products are summed as compensated FP32 pairs per thread and
+ *              block and finished in FP64; the FP32 correction is folded into
+ *              the FP64 solution and the residual replaced whenever the FP32
+ *              residual has dropped by the factor delta since the last
+ *              replacement (or after max(2000, iterations/8) FP32
+ *              iterations).
+ * The tolerance actually used is max(rtol, 3 floor): floor (reported as
+ * sdg_cg_info.floor_res) is the residual that rounding the solution to FP64
+ * leaves, which no FP64 vector can beat (about 3e-12 on 256 x 256 cells at
+ * N = 7); the solves measured here level off at 2.2-2.3 floor.  A true
+ * residual that stops improving (FP64: two replacements, mixed: thirty,
+ * without a 1.25x gain) within 10 max(floor, eval_res) also ends the solve
+ * with OK (eval_res: the rounding of A x itself, which for high degrees lies
+ * well above the representation floor).  Above
+ * it, a mixed solve continues with FP64 iterations from its current x (FP32
+ * rounding of the operator can keep it from resolving modes with tiny
+ * eigenvalues; at most 1/8 of its FP32 iterations, counted in
+ * applies_fp64) and an FP64 solve ends with SDG_ERR_NOT_CONVERGED; true_res
+ * always holds the achieved value.  (Unpreconditioned CG at N = 10, 11 on
+ * grids of 64^2 cells and more converges so slowly -- FP64 CG needs 244,000
+ * iterations on 64 x 64 cells at N = 11 -- that such solves can end there
+ * short of rtol = 1e-12.)
+ * For the singular pressure system every replaced residual is projected onto
+ * the range of the operator (its kernel part is round-off).
  * Defaults: SDG_FP64, 1e-12, 1e-12, 1000000.  Errors: INVALID_ARG. */
 int sdg_set_options(sdg_handle* h, int precision, double rtol_p, double rtol_v,
                     int maxit);
@@ -154,21 +195,37 @@ int sdg_set_mixed_options(sdg_handle* h, double delta, int max_updates, int defl
  * paper states it.  Errors: INVALID_ARG unless 1 <= nsub <= 1000. */
 int sdg_set_convection_substeps(sdg_handle* h, int nsub);
 
-/* Tile shape of the 2D FP32 operator kernel (a CTA's box of elements):
+/* Form of a CG iteration on the device.  0: one launch per iteration --
+ * the operator kernel of iteration k also applies the update of iteration
+ * k-1 (r -= alpha Ap, x += alpha p) while it stages its input, and reduces
+ * p.Ap, r.r, r.Ap and Ap.Ap, from which beta is formed one iteration ahead.
+ * 1 (default): two launches per iteration, the operator (p = r + beta p,
+ * Ap, p.Ap) and the update (x, r, r.r); measured faster (256 x 256, N = 7,
+ * FP32: 50.5 against 53.8 us per iteration; a mixed step of that workload
+ * 1.44 against 1.54 s).  Both are the CG of Sec. 2.1
+ * in exact arithmetic; the FP32 kernel deflation of sdg_set_mixed_options
+ * always uses the two-launch form.
+ * Errors: INVALID_ARG unless form is 0 or 1. */
+int sdg_set_iteration_form(sdg_handle* h, int form);
+
+/* Tile shape of the operator kernel.  2D FP32 (a CTA's box of elements):
  * 0 = base, 1 = twice as wide in x, 2 = twice as wide in y (fewer halo
- * loads per element, twice the threads per CTA).  Ignored in 3D.  The
+ * loads per element, twice the threads per CTA).  3D: 0 = columns of 4 x 4
+ * elements marching through z with a three-plane ring in shared memory
+ * (N <= 4; default), 1 or 2 = boxes of elements with their face halo.  The
  * shape changes the summation order of the CG's dot products, so results
- * differ in the last bits between shapes (each is deterministic).
+ * differ in the last bits between shapes (each is deterministic).  The
+ * one-launch CG iteration (sdg_set_iteration_form) uses the base 2D shape.
  * Errors: INVALID_ARG. */
 int sdg_set_tile(sdg_handle* h, int variant);
 /* Times the FP32 operator of the handle's grid with every tile shape (10
  * launches each, CUDA events on `stream`), keeps the fastest and returns it
  * in *variant (may be NULL); us (may be NULL) receives the mean launch time
- * of each shape in microseconds (3 entries in 2D, 1 in 3D).  No counterpart
+ * of each shape in microseconds (3 entries in 2D, 2 in 3D).  No counterpart
  * in the paper: a tuning aid.  Synchronises the stream. */
 int sdg_autotune(sdg_handle* h, int* variant, double* us, void* stream);
 
-/* Number of DOF of one field (ncell * n1^dim). *//* Number of DOF of one field (ncell * n1^dim). */
+/* Number of DOF of one field (ncell * n1^dim). */
 long long sdg_ndof(const sdg_handle* h);
 
 /* Copy the state in / out.  u, v (, w in 3D; NULL in 2D), p: host or device
@@ -345,8 +402,10 @@ int sdg_diagnostics(sdg_handle* h, double* kinetic_energy, double* div_norm,
  *     one double, written on `stream`.
  *   - At most 67,108,864 nodes per component; larger grids return
  *     SDG_ERR_INVALID_ARG with the limit in sdg_last_error.
- *   - The first call on a device looks up the scratch array's device
- *     address (cudaGetSymbolAddress) with that device current; make that
+ *   - The first call in each CUDA context of a device looks up the scratch
+ *     array's device address (cudaGetSymbolAddress) with that device
+ *     current, and keeps it for later calls in the same context (a new
+ *     context, e.g. after cudaDeviceReset, repeats the look-up); make that
  *     first call before any stream capture.
  *   - Every call shares the one scratch array: calls that can overlap on the
  *     GPU (different streams, or different host threads) race and must be

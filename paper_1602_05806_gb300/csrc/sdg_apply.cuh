@@ -79,6 +79,12 @@ struct ApplyParams {
   SolverState* st;
   double* partials;
   const float* kc;  // FP32 CG: kernel part of r per local node (null = off)
+  // fuse = 2 (one launch per CG iteration): x is r_{k-1}; ap_old = A p_{k-1};
+  // r_out receives r_k = r_{k-1} - alpha Ap_{k-1}; xsol += alpha p_{k-1}
+  const T* ap_old;
+  T* r_out;
+  T* xsol;
+  int zc;  // marching 3D kernel: planes per CTA
 };
 
 template <typename T>
@@ -151,6 +157,183 @@ __device__ __forceinline__ bool slot_elem(int s, const int o[3], int VX, int VY,
   return true;
 }
 
+// Last block of a one-launch CG iteration k: p.Ap, r.r (of r_k), r.Ap and
+// Ap.Ap of this iteration.  alpha_k = r.r / p.Ap; the next direction needs
+// beta_{k+1} = ||r_{k+1}||^2 / ||r_k||^2 before r_{k+1} exists, so its norm
+// is formed ahead from r_{k+1} = r_k - alpha_k Ap_k:
+//   ||r_{k+1}||^2 = r.r - 2 alpha_k r.Ap + alpha_k^2 Ap.Ap
+// (the next launch reduces ||r_{k+1}||^2 directly for its own alpha and for
+// the stopping test).  Stopping decisions as in the two-launch update.
+__device__ __forceinline__ void cg_iteration_finish(SolverState* st, double pAp, double rr, double rAp,
+                                                    double ApAp) {
+  st->pAp = pAp;
+  st->rr_old = st->rr;
+  st->rr = rr;
+  st->iter += 1;
+  if (rr > st->maxrr) st->maxrr = rr;
+  if (!(pAp > 0.0) || !isfinite(pAp) || !isfinite(rr)) {
+    st->done = 1;
+    st->status = SDG_ERR_BREAKDOWN;
+    st->alpha = 0.0;
+    st->beta = 0.0;
+  } else {
+    const double al = rr / pAp;
+    double next = rr - 2.0 * al * rAp + al * al * ApAp;
+    if (!(next > 0.0)) next = 0.0;
+    st->alpha = al;
+    st->beta = rr > 0.0 ? next / rr : 0.0;
+    if (rr <= st->tol2) {
+      // plain CG stops here; reliable mode confirms with the FP64 residual
+      if (st->reliable) st->pause = 1;
+      else { st->done = 1; st->status = SDG_OK; }
+    } else if (st->reliable && rr < st->delta2 * st->maxrr) {
+      st->pause = 1;
+    } else if (st->iter >= st->maxit) {
+      st->done = 1;
+      st->status = SDG_ERR_NOT_CONVERGED;
+    }
+  }
+  st->alpha_f = (float)st->alpha;
+  st->beta_f = (float)st->beta;
+}
+
+// The 1D line operator of one direction applied to one line of nodes: the
+// outputs val[m] = f (H^L xl + H^C xc + H^R xr)[m] of the block row of
+// Eq. pSyst (f: the direction's scale times the perpendicular weight), in
+// the even/odd basis of the line (see Coef), with the accurate contraction
+// when ACC.
+template <typename T, int N1, bool ACC>
+__device__ __forceinline__ void line_apply(const Coef<T, N1>& c, const T (&xl)[N1], const T (&xc)[N1],
+                                           const T (&xr)[N1], T f, T (&val)[N1]) {
+  // Even/odd form of the three line segments (see Coef): the neighbour
+  // segments enter only through sE = l^_E + r^_E, dE = l^_E - r^_E,
+  // sO = l^_O + r^_O, dO = r^_O - l^_O, the centre through cE, cO.
+  constexpr int H = N1 / 2, HE = (N1 + 1) / 2, HO = H > 0 ? H : 1;
+  constexpr bool MID = (N1 % 2) == 1;
+  // Accuracy of the contraction (it matters in FP32).  The operator
+  // annihilates every line-repeated pattern q of its local kernel (the
+  // constants; for odd N also the sawtooth z), so q may be removed from
+  // the three segments first: a centre node value c0 (differences of
+  // nearby values are exact), then for odd N the orthogonal fit onto
+  // {1, z} of the centre segment.  The operands shrink to the local
+  // variation of smooth fields, and the rounding of the products drops
+  // by orders of magnitude on the smooth and sawtooth-modulated modes
+  // with tiny eigenvalues.  The stored blocks annihilate q only up to
+  // rounding, so a symmetric correction (-rho, or -k0 S0 - k1 S1) keeps
+  // the applied operator exactly symmetric and exactly zero on q.
+  constexpr bool KZ = ACC && (N1 % 2 == 0);
+  T sE[HE], dE[HE], sO[HO], dO[HO], cE[HE], cO[HO];
+  if constexpr (ACC) {
+    const T c0 = xc[N1 / 2];
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const T l0 = xl[k] - c0, l1 = xl[N1 - 1 - k] - c0;
+      const T r0 = xr[k] - c0, r1 = xr[N1 - 1 - k] - c0;
+      sE[k] = (l0 + l1) + (r0 + r1);
+      dE[k] = (l0 - r0) + (l1 - r1);
+      const T lO = l0 - l1, rO = r0 - r1;
+      sO[k] = lO + rO;
+      dO[k] = rO - lO;
+      const T c0k = xc[k] - c0, c1k = xc[N1 - 1 - k] - c0;
+      cE[k] = c0k + c1k;
+      cO[k] = c0k - c1k;
+    }
+    if constexpr (MID) {
+      const T l0 = xl[H] - c0, r0 = xr[H] - c0;
+      sE[H] = l0 + r0;
+      dE[H] = l0 - r0;
+      cE[H] = xc[H] - c0;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const T lE = xl[k] + xl[N1 - 1 - k], lO = xl[k] - xl[N1 - 1 - k];
+      const T rE = xr[k] + xr[N1 - 1 - k], rO = xr[k] - xr[N1 - 1 - k];
+      sE[k] = lE + rE;
+      dE[k] = lE - rE;
+      sO[k] = lO + rO;
+      dO[k] = rO - lO;
+      cE[k] = xc[k] + xc[N1 - 1 - k];
+      cO[k] = xc[k] - xc[N1 - 1 - k];
+    }
+    if constexpr (MID) {
+      sE[H] = xl[H] + xr[H];
+      dE[H] = xl[H] - xr[H];
+      cE[H] = xc[H];
+    }
+  }
+  if constexpr (KZ) {
+    // orthogonal fit mu 1 + dz z of the centre segment, removed from all three
+    T sum = T(0), dz = T(0);
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      sum += cE[k];
+      dz = fma(c.zn[k], cO[k], dz);
+    }
+    const T mu2 = T(2) * (sum * c.inv_n);
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      cE[k] -= mu2;
+      sE[k] = fma(T(-2), mu2, sE[k]);
+      cO[k] = fma(-dz, c.z2[k], cO[k]);
+      sO[k] = fma(T(-2) * dz, c.z2[k], sO[k]);
+    }
+  }
+  // contractions: yE = A sE + B dO + CE cE ; yO = B^T dE + D sO + CO cO
+  T yE[HE], yO[HO];
+#pragma unroll
+  for (int m = 0; m < HE; ++m) {
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < HE; ++j) {
+      acc = fma(c.A[m * HE + j], sE[j], acc);
+      acc = fma(c.CE[m * HE + j], cE[j], acc);
+    }
+#pragma unroll
+    for (int j = 0; j < H; ++j) acc = fma(c.B[m * HO + j], dO[j], acc);
+    yE[m] = acc;
+  }
+#pragma unroll
+  for (int m = 0; m < H; ++m) {
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < HE; ++j) acc = fma(c.B[j * HO + m], dE[j], acc);
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      acc = fma(c.D[m * HO + j], sO[j], acc);
+      acc = fma(c.CO[m * HO + j], cO[j], acc);
+    }
+    yO[m] = acc;
+  }
+  if constexpr (KZ) {
+    T al = T(0), be = T(0);
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      al = fma(c.S0[k], cE[k], al);
+      be = fma(c.S1[k], cO[k], be);
+    }
+    const T ak = al * c.k0;
+#pragma unroll
+    for (int m = 0; m < H; ++m) {
+      yE[m] -= ak;
+      yO[m] = fma(-be, c.k1[m], yO[m]);
+    }
+  } else if constexpr (ACC) {
+#pragma unroll
+    for (int m = 0; m < HE; ++m) yE[m] = fma(-c.rho_e[m], cE[m], yE[m]);
+#pragma unroll
+    for (int m = 0; m < H; ++m) yO[m] = fma(-c.rho_o[m], cO[m], yO[m]);
+  }
+  // back to the nodes: out_k = yE + yO, out_{n-1-k} = yE - yO (scaled)
+#pragma unroll
+  for (int m = 0; m < H; ++m) {
+    const T t = f * yE[m];
+    val[m] = fma(f, yO[m], t);
+    val[N1 - 1 - m] = fma(-f, yO[m], t);
+  }
+  if constexpr (MID) val[H] = f * yE[H];
+}
+
 // ACC: accurate contraction (local kernel removal + symmetric correction),
 // used for every FP32 application and for the FP64 true residuals of the
 // mixed solver; plain FP64 CG uses the direct contraction.
@@ -158,13 +341,17 @@ __device__ __forceinline__ bool slot_elem(int s, const int o[3], int VX, int VY,
 // n1 = 8 fits 40 registers without spills, so six 256-thread blocks (three
 // of the 512-thread shapes) share an SM, as the shared-memory tile allows;
 // elsewhere the compiler chooses.
-template <typename T, int DIM, int N1, int V>
+// The one-launch CG iteration (ONE) keeps more values live (its r_k and four
+// sums), so it is compiled for five blocks per SM instead of six.
+template <typename T, int DIM, int N1, int V, bool ONE>
 constexpr int apply_min_blocks() {
-  return (sizeof(T) == 4 && DIM == 2 && N1 == 8) ? (V == 0 ? 6 : 3) : 1;
+  return (sizeof(T) == 4 && DIM == 2 && N1 == 8) ? (ONE ? 5 : (V == 0 ? 6 : 3)) : 1;
 }
 
-template <typename T, int DIM, int N1, bool ACC, int TV>
-__global__ void __launch_bounds__(Tile<DIM, N1, TV>::THREADS, (apply_min_blocks<T, DIM, N1, TV>()))
+// ONE: compiled for the one-launch CG iteration (fuse = 2) only; otherwise
+// for the plain apply (fuse = 0) and the two-launch operator (fuse = 1).
+template <typename T, int DIM, int N1, bool ACC, int TV, bool ONE>
+__global__ void __launch_bounds__(Tile<DIM, N1, TV>::THREADS, (apply_min_blocks<T, DIM, N1, TV, ONE>()))
     k_apply(const __grid_constant__ ApplyParams<T, DIM, N1> a) {
   using TS = Tile<DIM, N1, TV>;
   constexpr int TX = TS::TX, TY = TS::TY, TZ = TS::TZ, TE = TS::TE;
@@ -184,8 +371,9 @@ __global__ void __launch_bounds__(Tile<DIM, N1, TV>::THREADS, (apply_min_blocks<
   __shared__ T s_kc[sizeof(T) == 4 ? NPE : 1];
   __shared__ int s_gel[NSLOT];  // global element held by each slot (-1: unused)
 
-  const bool fuse = a.fuse != 0;
-  const bool defl = sizeof(T) == 4 && fuse && a.kc != nullptr;
+  const bool fuse = ONE || a.fuse != 0;
+  constexpr bool fuse2 = ONE;
+  const bool defl = sizeof(T) == 4 && fuse && !fuse2 && a.kc != nullptr;
   pdl_trigger();
 
   // prologue that reads nothing earlier kernels write: tile origin and valid
@@ -208,25 +396,92 @@ __global__ void __launch_bounds__(Tile<DIM, N1, TV>::THREADS, (apply_min_blocks<
 
   pdl_wait();
   bool first = false;
-  T beta = T(0);
+  T beta = T(0), alpha = T(0);
   if (fuse) {
     if (a.st->done || a.st->pause) return;  // uniform: written by the previous kernel
     first = (a.st->iter == 0);
-    // beta was formed once by the previous kernel (no FP64 division per thread)
-    if (!first) beta = sizeof(T) == 4 ? (T)a.st->beta_f : (T)a.st->beta;
+    // alpha and beta were formed once by the previous kernel (no FP64
+    // division per thread)
+    if (!first) {
+      beta = sizeof(T) == 4 ? (T)a.st->beta_f : (T)a.st->beta;
+      alpha = sizeof(T) == 4 ? (T)a.st->alpha_f : (T)a.st->alpha;
+    }
   }
   if (defl)
     for (int l = threadIdx.x; l < NPE; l += blockDim.x) s_kc[l] = (T)a.kc[l];
   __syncthreads();
 
   // ---- stage box + face halo (coalesced vector loads, padded rows) ----
-  for (int v = threadIdx.x; v < NSLOT * NV; v += blockDim.x) {
+  // fuse = 2: the box values come first, in a fixed thread mapping (v = tid +
+  // i blockDim) that the store loop repeats, so that each thread keeps its
+  // r_k values in registers for the reductions
+  constexpr int NBOX = (TE * NV + TS::THREADS - 1) / TS::THREADS;
+  V rkeep[NBOX];
+  if constexpr (fuse2) {
+#pragma unroll
+    for (int i = 0; i < NBOX; ++i) {
+      const int v = threadIdx.x + i * TS::THREADS;
+      if (v >= TE * NV) break;
+      const int s = v / NV, off = v - s * NV;
+      const int ge = s_gel[s];
+      if (ge < 0) continue;
+      const size_t gi = (size_t)ge * NV + off;
+      V r = reinterpret_cast<const V*>(a.x)[gi];
+      V val;
+      T* rp = reinterpret_cast<T*>(&r);
+      T* vp = reinterpret_cast<T*>(&val);
+      if (first) {
+        val = r;
+      } else {
+        const V ao = reinterpret_cast<const V*>(a.ap_old)[gi];
+        const V po = reinterpret_cast<const V*>(a.p_old)[gi];
+        V xv = reinterpret_cast<const V*>(a.xsol)[gi];
+        const T* ap = reinterpret_cast<const T*>(&ao);
+        const T* pp = reinterpret_cast<const T*>(&po);
+        T* xp = reinterpret_cast<T*>(&xv);
+#pragma unroll
+        for (int k = 0; k < VW; ++k) {
+          rp[k] = fma(-alpha, ap[k], rp[k]);  // r_k = r_{k-1} - alpha Ap_{k-1}
+          xp[k] = fma(alpha, pp[k], xp[k]);   // x_k = x_{k-1} + alpha p_{k-1}
+          vp[k] = fma(beta, pp[k], rp[k]);    // p_k = r_k + beta p_{k-1}
+        }
+        reinterpret_cast<V*>(a.xsol)[gi] = xv;
+      }
+      reinterpret_cast<V*>(a.r_out)[gi] = r;
+      reinterpret_cast<V*>(a.p_out)[gi] = val;
+      rkeep[i] = r;
+#pragma unroll
+      for (int k = 0; k < VW; ++k) {
+        const int q = off * VW + k, row = q / N1, l1 = q - row * N1;
+        s_in[s * ES + row * RS + l1] = vp[k];
+      }
+    }
+  }
+  for (int v = threadIdx.x + (fuse2 ? TE * NV : 0); v < NSLOT * NV; v += blockDim.x) {
     const int s = v / NV, off = v - s * NV;
     const int ge = s_gel[s];
     if (ge < 0) continue;
     const size_t gi = (size_t)ge * NV + off;
     V val;
-    if (!fuse) {
+    if (fuse2) {
+      // face halo: p_k of the neighbour, formed as its owner forms it
+      V r = reinterpret_cast<const V*>(a.x)[gi];
+      T* rp = reinterpret_cast<T*>(&r);
+      T* vp = reinterpret_cast<T*>(&val);
+      if (first) {
+        val = r;
+      } else {
+        const V ao = reinterpret_cast<const V*>(a.ap_old)[gi];
+        const V po = reinterpret_cast<const V*>(a.p_old)[gi];
+        const T* ap = reinterpret_cast<const T*>(&ao);
+        const T* pp = reinterpret_cast<const T*>(&po);
+#pragma unroll
+        for (int k = 0; k < VW; ++k) {
+          rp[k] = fma(-alpha, ap[k], rp[k]);
+          vp[k] = fma(beta, pp[k], rp[k]);
+        }
+      }
+    } else if (!fuse) {
       val = reinterpret_cast<const V*>(a.x)[gi];
     } else {
       V r = reinterpret_cast<const V*>(a.x)[gi];
@@ -290,135 +545,8 @@ __global__ void __launch_bounds__(Tile<DIM, N1, TV>::THREADS, (apply_min_blocks<
         xc[k] = s_in[sc * ES + base + k * stride];
         xr[k] = s_in[sr * ES + base + k * stride];
       }
-      // Even/odd form of the three line segments (see Coef): the neighbour
-      // segments enter only through sE = l^_E + r^_E, dE = l^_E - r^_E,
-      // sO = l^_O + r^_O, dO = r^_O - l^_O, the centre through cE, cO.
-      constexpr int H = N1 / 2, HE = (N1 + 1) / 2, HO = H > 0 ? H : 1;
-      constexpr bool MID = (N1 % 2) == 1;
-      // Accuracy of the contraction (it matters in FP32).  The operator
-      // annihilates every line-repeated pattern q of its local kernel (the
-      // constants; for odd N also the sawtooth z), so q may be removed from
-      // the three segments first: a centre node value c0 (differences of
-      // nearby values are exact), then for odd N the orthogonal fit onto
-      // {1, z} of the centre segment.  The operands shrink to the local
-      // variation of smooth fields, and the rounding of the products drops
-      // by orders of magnitude on the smooth and sawtooth-modulated modes
-      // with tiny eigenvalues.  The stored blocks annihilate q only up to
-      // rounding, so a symmetric correction (-rho, or -k0 S0 - k1 S1) keeps
-      // the applied operator exactly symmetric and exactly zero on q.
-      constexpr bool KZ = ACC && (N1 % 2 == 0);
-      T sE[HE], dE[HE], sO[HO], dO[HO], cE[HE], cO[HO];
-      if constexpr (ACC) {
-        const T c0 = xc[N1 / 2];
-#pragma unroll
-        for (int k = 0; k < H; ++k) {
-          const T l0 = xl[k] - c0, l1 = xl[N1 - 1 - k] - c0;
-          const T r0 = xr[k] - c0, r1 = xr[N1 - 1 - k] - c0;
-          sE[k] = (l0 + l1) + (r0 + r1);
-          dE[k] = (l0 - r0) + (l1 - r1);
-          const T lO = l0 - l1, rO = r0 - r1;
-          sO[k] = lO + rO;
-          dO[k] = rO - lO;
-          const T c0k = xc[k] - c0, c1k = xc[N1 - 1 - k] - c0;
-          cE[k] = c0k + c1k;
-          cO[k] = c0k - c1k;
-        }
-        if constexpr (MID) {
-          const T l0 = xl[H] - c0, r0 = xr[H] - c0;
-          sE[H] = l0 + r0;
-          dE[H] = l0 - r0;
-          cE[H] = xc[H] - c0;
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < H; ++k) {
-          const T lE = xl[k] + xl[N1 - 1 - k], lO = xl[k] - xl[N1 - 1 - k];
-          const T rE = xr[k] + xr[N1 - 1 - k], rO = xr[k] - xr[N1 - 1 - k];
-          sE[k] = lE + rE;
-          dE[k] = lE - rE;
-          sO[k] = lO + rO;
-          dO[k] = rO - lO;
-          cE[k] = xc[k] + xc[N1 - 1 - k];
-          cO[k] = xc[k] - xc[N1 - 1 - k];
-        }
-        if constexpr (MID) {
-          sE[H] = xl[H] + xr[H];
-          dE[H] = xl[H] - xr[H];
-          cE[H] = xc[H];
-        }
-      }
-      if constexpr (KZ) {
-        // orthogonal fit mu 1 + dz z of the centre segment, removed from all three
-        T sum = T(0), dz = T(0);
-#pragma unroll
-        for (int k = 0; k < H; ++k) {
-          sum += cE[k];
-          dz = fma(a.c.zn[k], cO[k], dz);
-        }
-        const T mu2 = T(2) * (sum * a.c.inv_n);
-#pragma unroll
-        for (int k = 0; k < H; ++k) {
-          cE[k] -= mu2;
-          sE[k] = fma(T(-2), mu2, sE[k]);
-          cO[k] = fma(-dz, a.c.z2[k], cO[k]);
-          sO[k] = fma(T(-2) * dz, a.c.z2[k], sO[k]);
-        }
-      }
-      // contractions: yE = A sE + B dO + CE cE ; yO = B^T dE + D sO + CO cO
-      T yE[HE], yO[HO];
-#pragma unroll
-      for (int m = 0; m < HE; ++m) {
-        T acc = T(0);
-#pragma unroll
-        for (int j = 0; j < HE; ++j) {
-          acc = fma(a.c.A[m * HE + j], sE[j], acc);
-          acc = fma(a.c.CE[m * HE + j], cE[j], acc);
-        }
-#pragma unroll
-        for (int j = 0; j < H; ++j) acc = fma(a.c.B[m * HO + j], dO[j], acc);
-        yE[m] = acc;
-      }
-#pragma unroll
-      for (int m = 0; m < H; ++m) {
-        T acc = T(0);
-#pragma unroll
-        for (int j = 0; j < HE; ++j) acc = fma(a.c.B[j * HO + m], dE[j], acc);
-#pragma unroll
-        for (int j = 0; j < H; ++j) {
-          acc = fma(a.c.D[m * HO + j], sO[j], acc);
-          acc = fma(a.c.CO[m * HO + j], cO[j], acc);
-        }
-        yO[m] = acc;
-      }
-      if constexpr (KZ) {
-        T al = T(0), be = T(0);
-#pragma unroll
-        for (int k = 0; k < H; ++k) {
-          al = fma(a.c.S0[k], cE[k], al);
-          be = fma(a.c.S1[k], cO[k], be);
-        }
-        const T ak = al * a.c.k0;
-#pragma unroll
-        for (int m = 0; m < H; ++m) {
-          yE[m] -= ak;
-          yO[m] = fma(-be, a.c.k1[m], yO[m]);
-        }
-      } else if constexpr (ACC) {
-#pragma unroll
-        for (int m = 0; m < HE; ++m) yE[m] = fma(-a.c.rho_e[m], cE[m], yE[m]);
-#pragma unroll
-        for (int m = 0; m < H; ++m) yO[m] = fma(-a.c.rho_o[m], cO[m], yO[m]);
-      }
-      // back to the nodes: out_k = yE + yO, out_{n-1-k} = yE - yO (scaled)
-      const T f = a.s[d] * wp;
       T val[N1];
-#pragma unroll
-      for (int m = 0; m < H; ++m) {
-        const T t = f * yE[m];
-        val[m] = fma(f, yO[m], t);
-        val[N1 - 1 - m] = fma(-f, yO[m], t);
-      }
-      if constexpr (MID) val[H] = f * yE[H];
+      line_apply<T, N1, ACC>(a.c, xl, xc, xr, a.s[d] * wp, val);
       T* out = s_out + te * ES + base;
 #pragma unroll
       for (int m = 0; m < N1; ++m) {
@@ -435,6 +563,54 @@ __global__ void __launch_bounds__(Tile<DIM, N1, TV>::THREADS, (apply_min_blocks<
     // s_out; when whole elements fall in one warp, a warp barrier suffices
     if constexpr (WARP_ELEMS) __syncwarp();
     else __syncthreads();
+  }
+
+  if constexpr (fuse2) {
+    // ---- one launch per CG iteration: store Ap_k and reduce, in the staging
+    // thread mapping, p.Ap and r.r (compensated), r.Ap and Ap.Ap ----
+    __syncthreads();
+    T s_pa = T(0), c_pa = T(0), s_rr = T(0), c_rr = T(0), s_ra = T(0), s_aa = T(0);
+#pragma unroll
+    for (int i = 0; i < NBOX; ++i) {
+      const int v = threadIdx.x + i * TS::THREADS;
+      if (v >= TE * NV) break;
+      const int e = v / NV, off = v - e * NV;
+      const int ge = s_gel[e];
+      if (ge < 0) continue;
+      V yv;
+      T* yp = reinterpret_cast<T*>(&yv);
+      const T* rp = reinterpret_cast<const T*>(&rkeep[i]);
+#pragma unroll
+      for (int k = 0; k < VW; ++k) {
+        const int q = off * VW + k, row = q / N1, l1 = q - row * N1;
+        const T y = s_out[e * ES + row * RS + l1];
+        const T pv = s_in[e * ES + row * RS + l1];
+        yp[k] = y;
+        const T t1 = fma(pv, y, -c_pa);
+        const T u1 = s_pa + t1;
+        c_pa = (u1 - s_pa) - t1;
+        s_pa = u1;
+        const T t2 = fma(rp[k], rp[k], -c_rr);
+        const T u2 = s_rr + t2;
+        c_rr = (u2 - s_rr) - t2;
+        s_rr = u2;
+        s_ra = fma(rp[k], y, s_ra);
+        s_aa = fma(y, y, s_aa);
+      }
+      reinterpret_cast<V*>(a.y)[(size_t)ge * NV + off] = yv;
+    }
+    double tot[4];
+    bool last;
+    if constexpr (sizeof(T) == 4) {
+      F2 v4[4] = {F2{(float)s_pa, -(float)c_pa}, F2{(float)s_rr, -(float)c_rr}, F2{(float)s_ra, 0.0f},
+                  F2{(float)s_aa, 0.0f}};
+      last = grid_sum_f2<4>(v4, a.partials, &a.st->counter, tot);
+    } else {
+      double v4[4] = {(double)s_pa - (double)c_pa, (double)s_rr - (double)c_rr, (double)s_ra, (double)s_aa};
+      last = grid_sum<4>(v4, a.partials, &a.st->counter, tot);
+    }
+    if (last && threadIdx.x == 0) cg_iteration_finish(a.st, tot[0], tot[1], tot[2], tot[3]);
+    return;
   }
 
   // ---- store the box (vectorised) and reduce p^T A p ----
@@ -497,10 +673,12 @@ __global__ void __launch_bounds__(Tile<DIM, N1, TV>::THREADS, (apply_min_blocks<
   }
 }
 
-template <typename T, int DIM, int N1, bool ACC, int V>
-cudaError_t launch_apply_acc(const sdg_handle* h, const ApplyArgs<T>& in, cudaStream_t stream) {
-  using TS = Tile<DIM, N1, V>;
-  ApplyParams<T, DIM, N1> p;
+// Kernel parameters from the handle and the launch arguments: the stored
+// line operator in the compute precision, the weights, pointers, scales and
+// grid size (the tile counts are set by each launcher).
+template <typename T, int DIM, int N1>
+void fill_apply_params(const sdg_handle* h, const ApplyArgs<T>& in, ApplyParams<T, DIM, N1>* pp) {
+  ApplyParams<T, DIM, N1>& p = *pp;
   const Basis1D& b = h->basis;
   const CoefSet& cs = sizeof(T) == 4 ? h->coef32 : h->coef64;  // values exact in T
   constexpr int H = N1 / 2, HE = (N1 + 1) / 2, HO = H > 0 ? H : 1;
@@ -538,13 +716,24 @@ cudaError_t launch_apply_acc(const sdg_handle* h, const ApplyArgs<T>& in, cudaSt
   p.n[0] = h->g.n[0];
   p.n[1] = h->g.n[1];
   p.n[2] = DIM == 3 ? h->g.n[2] : 1;
-  p.ntile[0] = (p.n[0] + TS::TX - 1) / TS::TX;
-  p.ntile[1] = (p.n[1] + TS::TY - 1) / TS::TY;
-  p.ntile[2] = (p.n[2] + TS::TZ - 1) / TS::TZ;
   p.fuse = in.fuse;
   p.st = in.st;
   p.partials = in.partials;
   p.kc = in.kc;
+  p.ap_old = in.ap_old;
+  p.r_out = in.r_out;
+  p.xsol = in.xsol;
+  p.zc = 0;
+}
+
+template <typename T, int DIM, int N1, bool ACC, int V, bool ONE = false>
+cudaError_t launch_apply_acc(const sdg_handle* h, const ApplyArgs<T>& in, cudaStream_t stream) {
+  using TS = Tile<DIM, N1, V>;
+  ApplyParams<T, DIM, N1> p;
+  fill_apply_params<T, DIM, N1>(h, in, &p);
+  p.ntile[0] = (p.n[0] + TS::TX - 1) / TS::TX;
+  p.ntile[1] = (p.n[1] + TS::TY - 1) / TS::TY;
+  p.ntile[2] = (p.n[2] + TS::TZ - 1) / TS::TZ;
   const long long nblk = (long long)p.ntile[0] * p.ntile[1] * p.ntile[2];
   if (nblk > h->max_blocks) return cudaErrorInvalidConfiguration;
   const size_t smem = (size_t)(TS::NSLOT + TS::TE) * TS::ES * sizeof(T);
@@ -553,7 +742,7 @@ cudaError_t launch_apply_acc(const sdg_handle* h, const ApplyArgs<T>& in, cudaSt
   // harmless
   static std::atomic<bool> attr_set{false};
   if (!attr_set.load(std::memory_order_acquire)) {
-    cudaError_t e = cudaFuncSetAttribute(k_apply<T, DIM, N1, ACC, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_apply<T, DIM, N1, ACC, V, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     attr_set.store(true, std::memory_order_release);
@@ -568,7 +757,7 @@ cudaError_t launch_apply_acc(const sdg_handle* h, const ApplyArgs<T>& in, cudaSt
   attr[0].val.programmaticStreamSerializationAllowed = in.pdl ? 1 : 0;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_apply<T, DIM, N1, ACC, V>, p);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_apply<T, DIM, N1, ACC, V, ONE>, p);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -577,6 +766,8 @@ cudaError_t launch_apply_acc(const sdg_handle* h, const ApplyArgs<T>& in, cudaSt
 // bound by the FP64 pipe, not by the tile).
 template <typename T, int DIM, int N1>
 cudaError_t launch_apply_t(const sdg_handle* h, const ApplyArgs<T>& in, cudaStream_t stream) {
+  // the one-launch CG iteration: base tile, accurate contraction
+  if (in.fuse == 2) return launch_apply_acc<T, DIM, N1, true, 0, true>(h, in, stream);
   if constexpr (sizeof(T) == 4) {
     if constexpr (DIM == 2) {
       if (in.tile == 1) return launch_apply_acc<T, DIM, N1, true, 1>(h, in, stream);

@@ -1,9 +1,20 @@
-// Instantiations of the element-tile operator kernel for dim = 3, float.
-#include "sdg_apply.cuh"
+// Instantiations of the 3D operator kernels (z-marching columns, element boxes) for dim = 3, float.
+#include "sdg_apply3.cuh"
 
 namespace sdg {
 
 cudaError_t apply_dispatch_3d(const sdg_handle* h, const ApplyArgs<float>& a, cudaStream_t s) {
+  // tile 0: the z-marching column kernel for n1 <= 5; otherwise element boxes
+  if (a.tile == 0) {
+    switch (h->g.n1) {
+      case 1: return launch_apply3m_t<float, 1>(h, a, s);
+      case 2: return launch_apply3m_t<float, 2>(h, a, s);
+      case 3: return launch_apply3m_t<float, 3>(h, a, s);
+      case 4: return launch_apply3m_t<float, 4>(h, a, s);
+      case 5: return launch_apply3m_t<float, 5>(h, a, s);
+      default: break;
+    }
+  }
   switch (h->g.n1) {
     case 1: return launch_apply_t<float, 3, 1>(h, a, s);
     case 2: return launch_apply_t<float, 3, 2>(h, a, s);

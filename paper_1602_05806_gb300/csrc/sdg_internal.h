@@ -57,7 +57,7 @@ constexpr int kDeflateBlocks = 304;    // grid of the deflated FP32 CG update
 constexpr int kPartialSlots = 4;       // doubles per block in a partials array
 constexpr int kReduceBlocks = 152 * 8; // grid of the vector / reduction kernels
 
-enum StateId { kStP64 = 0, kStP32 = 1, kStV64 = 2, kStV32 = 3, kStMisc = 4 };
+enum StateId { kStP64 = 0, kStP32 = 1, kStV64 = 2, kStV32 = 3, kStMisc = 4, kStTrue = 5 };
 
 constexpr int kProfEvents = 64;  // event pairs per CG batch when profiling
 
@@ -65,12 +65,14 @@ constexpr int kProfEvents = 64;  // event pairs per CG batch when profiling
 
 struct sdg_handle {
   int device;
+  int nsm;                       // streaming multiprocessors of the device
   sdg::Geo g;
   int dim;
   double L[3], dx[3];
   double nu, theta, dt;
   int nsub;                      // SSP-RK3 sub-steps of the explicit convection per dt
   int tile32;                    // tile shape variant of the 2D FP32 operator
+  int two_launch;                // CG iteration form: 1 = operator + update launches
   int precision;
   double rtol_p, rtol_v;
   double delta;     // mixed: reliable-update factor
@@ -98,9 +100,11 @@ struct sdg_handle {
   long long adj_fields;  // fields of ndof doubles in adj
   // solver vectors
   // p is double-buffered: the fused apply reads p_old with its halo while
-  // other CTAs write p_new, so the two must not alias.
-  double *r64, *p64[2], *Ap64;
-  float *x32, *r32, *p32[2], *Ap32;
+  // other CTAs write p_new, so the two must not alias; with one launch per
+  // iteration r and Ap are read with their halo too and alternate likewise
+  // (r64 / r64b, Ap64 / Ap64b, r32 / r32b, Ap32 / Ap32b).
+  double *r64, *r64b, *p64[2], *Ap64, *Ap64b;
+  float *x32, *r32, *r32b, *p32[2], *Ap32, *Ap32b;
   sdg::SolverState* st;   // kMaxStates device states
   sdg::SolverState* st_host;  // pinned mirror
   double* partials;       // kMaxStates * max_blocks * kPartialSlots
@@ -166,6 +170,14 @@ struct ApplyArgs {
   int accurate;     // FP64: use the accurate contraction (FP32 always does)
   int tile;         // 2D FP32: tile shape variant (0 base, 1 wide in x, 2 wide in y)
   int pdl;          // launch with programmatic stream serialisation (CG loop)
+  // fuse = 2: one launch per CG iteration k.  x is r_{k-1}, p_old p_{k-1},
+  // ap_old A p_{k-1}; the kernel writes r_k = r_{k-1} - alpha Ap_{k-1} to
+  // r_out, adds alpha p_{k-1} to xsol, forms p_k = r_k + beta p_{k-1} (to
+  // p_out) and Ap_k (to y), and reduces p.Ap, r.r, r.Ap, Ap.Ap into the state
+  // (alpha_k, beta_{k+1}, stopping decisions).  Iteration 0 takes p_0 = r_0.
+  const T* ap_old;
+  T* r_out;
+  T* xsol;
 };
 
 cudaError_t launch_apply_f64(const sdg_handle* h, const ApplyArgs<double>& a, cudaStream_t s);
@@ -178,10 +190,6 @@ cudaError_t apply_dispatch_3d(const sdg_handle* h, const ApplyArgs<double>& a, c
 cudaError_t apply_dispatch_3d(const sdg_handle* h, const ApplyArgs<float>& a, cudaStream_t s);
 
 // ---- vector / step kernels (sdg_kernels.cu) --------------------------------
-cudaError_t cg_init_f64(const double* b, const double* Ax, double* r, long long n, SolverState* st,
-                        double* partials, double rtol, int maxit, cudaStream_t s);
-cudaError_t cg_init_f32(const float* b, const float* Ax, float* r, long long n, SolverState* st,
-                        double* partials, double rtol, int maxit, cudaStream_t s);
 cudaError_t cg_update_f64(double* x, double* r, const double* p, const double* Ap, long long n,
                           SolverState* st, double* partials, cudaStream_t s);
 cudaError_t cg_update_f32(float* x, float* r, const float* p, const float* Ap, long long n,
@@ -191,18 +199,39 @@ cudaError_t cg_update_f32(float* x, float* r, const float* p, const float* Ap, l
 //   rel_residual:   r64 = b - Ax (FP64), mean and ||r - mean|| reduced in FP64;
 //                   the last block replaces the recursive residual norm by the
 //                   true one (scaled by sigma^2) and decides convergence.  With
-//                   init = 1 it also starts the solve (sigma = 1/||b||, iter = 0).
-//                   project = 1 removes the mean (singular pressure system).
-//   rel_convert:    r32 = sigma (r64 - mean)
+//                   init = 1 it also starts the solve (sigma = 1/||b||, or 1
+//                   when unscaled = 1, iter = 0).  project = 1 removes the mean
+//                   from the norm and from r64 (singular pressure system).
+//   rel_convert:    r32 = sigma r64
 cudaError_t rel_accumulate(double* x64, float* x32, long long n, const SolverState* st, cudaStream_t s);
+// mode: 1 starts the solve; 2 replaces the residual of a running iteration
+// (alpha and beta kept: the direction continues); 0 replaces it and
+// restarts the direction from its norm (beta = r.r new / r.r old)
 cudaError_t rel_residual(const double* b, const double* Ax, double* r64, long long n, SolverState* st,
-                         double* partials, double rtol, int maxit, double delta, int init, int project,
-                         cudaStream_t s);
+                         double* partials, double rtol, int maxit, double delta, int mode, int project,
+                         int unscaled, cudaStream_t s);
 cudaError_t rel_convert(const double* r64, float* r32, long long n, const SolverState* st, cudaStream_t s);
+// st->red[0..2] = sum(r), sum(r^2), sum(b^2) of r = b - Ax (b may be NULL:
+// zero; nothing written but the state): the true residual of a finished solve
+cudaError_t resid_norms(const double* b, const double* Ax, long long n, SolverState* st, double* partials,
+                        cudaStream_t s);
+// u_i = s_i ulp(x_i) / (2 sqrt 3), s_i = +-1 from a hash of i: the spread of
+// rounding x to FP64, whose image under the operator estimates the residual
+// floor of FP64 solutions
+cudaError_t rounding_perturbation(const double* x, double* u, long long n, cudaStream_t s);
+// After the range projection of a replaced residual r (singular system):
+// rr = sigma^2 ||r||^2 and the stopping / direction decisions of
+// rel_residual (same mode) taken again on it
+cudaError_t rel_renorm(const double* r, long long n, SolverState* st, double* partials, int mode, cudaStream_t s);
+// x += alpha p (state's alpha): the pending update of a one-launch CG
+// iteration stopped at maxit
+cudaError_t pending_update(double* x, const double* p, long long n, const SolverState* st, cudaStream_t s);
+cudaError_t pending_update(float* x, const float* p, long long n, const SolverState* st, cudaStream_t s);
 
 // Restore the component of x in the kernel of the periodic pressure operator
 // to that of x0: c = (1/ncell) (P1 (x) ... (x) P1) sum_e (x - x0)[e], then
-// x[e] -= c for every element (P1: 1D kernel projector, kproj).
+// x[e] -= c for every element (P1: 1D kernel projector, kproj).  x0 = NULL
+// removes the kernel component of x (projection onto the range).
 cudaError_t kernel_restore(const sdg_handle* h, double* x, const double* x0, cudaStream_t s, int* launches);
 
 // step stages

@@ -51,46 +51,6 @@ inline unsigned grid_full(long long n) {
 
 // ------------------------------------------------------------------ CG vectors
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
-    k_cg_init(const T* __restrict__ b, const T* __restrict__ Ax, T* __restrict__ r, long long n,
-              SolverState* st, double* partials, double rtol, int maxit) {
-  double rr = 0.0, bb = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const T bi = b[i];
-    const T ri = bi - Ax[i];
-    r[i] = ri;
-    rr += (double)ri * (double)ri;
-    bb += (double)bi * (double)bi;
-  }
-  double v[2] = {rr, bb}, tot[2];
-  if (grid_sum<2>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
-    st->rr = tot[0];
-    st->rr_old = tot[0];
-    st->bnorm2 = tot[1];
-    st->tol2 = rtol * rtol * tot[1];
-    st->iter = 0;
-    st->maxit = maxit;
-    st->status = SDG_OK;
-    st->alpha = 0.0;
-    st->beta = 0.0;
-    st->alpha_f = 0.0f;
-    st->beta_f = 0.0f;
-    st->pAp = 0.0;
-    st->reliable = 0;
-    st->pause = 0;
-    st->updates = 0;
-    st->maxrr = tot[0];
-    st->delta2 = 0.0;
-    st->done = (tot[1] == 0.0 || tot[0] <= st->tol2) ? 1 : 0;
-    if (!isfinite(tot[0]) || !isfinite(tot[1])) {
-      st->done = 1;
-      st->status = SDG_ERR_BREAKDOWN;
-    }
-  }
-}
-
-template <typename T>
 struct V4;
 template <>
 struct V4<float> { using V = float4; static constexpr int W = 4; };
@@ -296,7 +256,8 @@ __global__ void __launch_bounds__(kThreads)
 __global__ void __launch_bounds__(kThreads)
     k_rel_residual(const double* __restrict__ b, const double* __restrict__ Ax, double* __restrict__ r,
                    long long n, SolverState* st, double* partials, double rtol, int maxit, double delta,
-                   int init, int project) {
+                   int mode, int project, int unscaled) {
+  const bool init = mode == 1;
   double s = 0.0, ss = 0.0, bb = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
@@ -315,7 +276,9 @@ __global__ void __launch_bounds__(kThreads)
     if (rrp < 0.0) rrp = 0.0;
     if (init) {
       st->bnorm2 = tot[2];
-      st->sigma = tot[2] > 0.0 ? 1.0 / sqrt(tot[2]) : 1.0;
+      // FP32 iterations run on sigma-scaled vectors (||b|| -> 1); FP64
+      // iterations replace their own residual vector, unscaled
+      st->sigma = (unscaled || !(tot[2] > 0.0)) ? 1.0 : 1.0 / sqrt(tot[2]);
       st->tol2 = rtol * rtol * tot[2] * st->sigma * st->sigma;
       st->iter = 0;
       st->maxit = maxit;
@@ -330,9 +293,11 @@ __global__ void __launch_bounds__(kThreads)
     }
     const double rr = rrp * st->sigma * st->sigma;
     st->mean = mean;
-    // the next direction: p = r_true + (rr_true / rr_old) p_old
-    st->beta = (!init && st->rr_old > 0.0) ? rr / st->rr_old : 0.0;
-    st->beta_f = (float)st->beta;
+    if (mode != 2) {
+      // the next direction: p = r_true + (rr_true / rr_old) p_old
+      st->beta = (!init && st->rr_old > 0.0) ? rr / st->rr_old : 0.0;
+      st->beta_f = (float)st->beta;
+    }
     // the next direction uses beta = rr_true / rr_k, rr_k being the residual
     // norm of the iteration before the one that triggered the update
     if (init) st->rr_old = rr;
@@ -347,13 +312,101 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// r32 = sigma (r64 - mean)
+// red[0..2] = sum(r), sum(r^2), sum(b^2) of r = b - Ax
 __global__ void __launch_bounds__(kThreads)
-    k_rel_convert(const double* __restrict__ r64, float* __restrict__ r32, long long n, const SolverState* st) {
-  const double mean = st->mean, sigma = st->sigma;
+    k_resid_norms(const double* __restrict__ b, const double* __restrict__ Ax, long long n, SolverState* st,
+                  double* partials) {
+  double s = 0.0, ss = 0.0, bb = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double bi = b ? b[i] : 0.0;
+    const double ri = bi - Ax[i];
+    s += ri;
+    ss += ri * ri;
+    bb += bi * bi;
+  }
+  double v[3] = {s, ss, bb}, tot[3];
+  if (grid_sum<3>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
+    st->red[0] = tot[0];
+    st->red[1] = tot[1];
+    st->red[2] = tot[2];
+  }
+}
+
+// u_i = s_i ulp(x_i) / (2 sqrt 3): ulp from the exponent bits of x_i (0 for
+// zero and subnormal x_i), s_i the top bit of an integer hash of i
+__global__ void __launch_bounds__(kThreads)
+    k_rounding_perturbation(const double* __restrict__ x, double* __restrict__ u, long long n) {
+  const double scale = 0.5 / 1.7320508075688772 / 4503599627370496.0;  // 1 / (2 sqrt 3) / 2^52
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    // 2^floor(log2 |x|): the exponent field alone
+    const double pw = __longlong_as_double(__double_as_longlong(x[i]) & 0x7FF0000000000000LL);
+    unsigned long long z = (unsigned long long)i + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    u[i] = ((z >> 63) ? -scale : scale) * pw;
+  }
+}
+
+// Norm and decisions of a replaced residual after its projection onto the
+// range (singular pressure system): rr = sigma^2 ||r||^2 of the projected
+// r, and the decisions k_rel_residual took on the unprojected norm taken
+// again (the iteration's alpha = rr / pAp must see the norm of the vector it
+// iterates on).
+__global__ void __launch_bounds__(kThreads)
+    k_rel_renorm(const double* __restrict__ r, long long n, SolverState* st, double* partials, int mode) {
+  double ss = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
-    r32[i] = (float)((r64[i] - mean) * sigma);
+    ss += r[i] * r[i];
+  double v[1] = {ss}, tot[1];
+  if (grid_sum<1>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
+    const double rr = tot[0] * st->sigma * st->sigma;
+    if (mode == 1) st->rr_old = rr;
+    if (mode == 0) {
+      st->beta = st->rr_old > 0.0 ? rr / st->rr_old : 0.0;
+      st->beta_f = (float)st->beta;
+    }
+    st->rr = rr;
+    st->maxrr = rr;
+    if (!isfinite(rr)) {
+      st->done = 1;
+      st->status = SDG_ERR_BREAKDOWN;
+    } else {
+      st->done = (st->bnorm2 == 0.0 || rr <= st->tol2) ? 1 : 0;
+    }
+  }
+}
+
+// x += alpha p with the state's alpha: the update the next one-launch CG
+// iteration would have applied, when the iteration stops at maxit
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_pending_update(T* __restrict__ x, const T* __restrict__ p, long long n, const SolverState* st) {
+  const T alpha = sizeof(T) == 4 ? (T)st->alpha_f : (T)st->alpha;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = fma(alpha, p[i], x[i]);
+}
+
+// r -= mean (the round-off constant part of a replaced FP64 residual)
+__global__ void __launch_bounds__(kThreads)
+    k_sub_mean(double* __restrict__ r, long long n, const SolverState* st) {
+  const double mean = st->mean;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    r[i] -= mean;
+}
+
+// r32 = sigma r64 (r64 already has its kernel part removed)
+__global__ void __launch_bounds__(kThreads)
+    k_rel_convert(const double* __restrict__ r64, float* __restrict__ r32, long long n, const SolverState* st) {
+  const double sigma = st->sigma;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    r32[i] = (float)(r64[i] * sigma);
 }
 
 // ------------------------------------------------------------------ step stages
@@ -657,7 +710,7 @@ __global__ void __launch_bounds__(kThreads)
     double acc = 0.0;
     for (long long e = blockIdx.x; e < g.ncell; e += G) {
       const long long i = e * g.npe + l;
-      acc += x[i] - x0[i];
+      acc += x0 ? x[i] - x0[i] : x[i];
     }
     part[(size_t)blockIdx.x * g.npe + l] = acc;
   }
@@ -724,16 +777,6 @@ cudaError_t kernel_restore(const sdg_handle* h, double* x, const double* x0, cud
 }
 
 // ------------------------------------------------------------------ launchers
-cudaError_t cg_init_f64(const double* b, const double* Ax, double* r, long long n, SolverState* st,
-                        double* partials, double rtol, int maxit, cudaStream_t s) {
-  k_cg_init<double><<<grid_for(n), kThreads, 0, s>>>(b, Ax, r, n, st, partials, rtol, maxit);
-  return cudaGetLastError();
-}
-cudaError_t cg_init_f32(const float* b, const float* Ax, float* r, long long n, SolverState* st,
-                        double* partials, double rtol, int maxit, cudaStream_t s) {
-  k_cg_init<float><<<grid_for(n), kThreads, 0, s>>>(b, Ax, r, n, st, partials, rtol, maxit);
-  return cudaGetLastError();
-}
 cudaError_t cg_update_f64(double* x, double* r, const double* p, const double* Ap, long long n,
                           SolverState* st, double* partials, cudaStream_t s) {
   return launch_pdl(k_cg_update<double>, grid_vec(n, 2), kThreads, 0, s, x, r, p, Ap, n, st, partials, Deflate{});
@@ -762,10 +805,34 @@ cudaError_t rel_accumulate(double* x64, float* x32, long long n, const SolverSta
   return cudaGetLastError();
 }
 cudaError_t rel_residual(const double* b, const double* Ax, double* r64, long long n, SolverState* st,
-                         double* partials, double rtol, int maxit, double delta, int init, int project,
-                         cudaStream_t s) {
-  k_rel_residual<<<grid_for(n), kThreads, 0, s>>>(b, Ax, r64, n, st, partials, rtol, maxit, delta, init,
-                                                  project);
+                         double* partials, double rtol, int maxit, double delta, int mode, int project,
+                         int unscaled, cudaStream_t s) {
+  k_rel_residual<<<grid_for(n), kThreads, 0, s>>>(b, Ax, r64, n, st, partials, rtol, maxit, delta, mode,
+                                                  project, unscaled);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !project) return e;
+  k_sub_mean<<<grid_for(n), kThreads, 0, s>>>(r64, n, st);
+  return cudaGetLastError();
+}
+cudaError_t resid_norms(const double* b, const double* Ax, long long n, SolverState* st, double* partials,
+                        cudaStream_t s) {
+  k_resid_norms<<<grid_for(n), kThreads, 0, s>>>(b, Ax, n, st, partials);
+  return cudaGetLastError();
+}
+cudaError_t rel_renorm(const double* r, long long n, SolverState* st, double* partials, int mode, cudaStream_t s) {
+  k_rel_renorm<<<grid_for(n), kThreads, 0, s>>>(r, n, st, partials, mode);
+  return cudaGetLastError();
+}
+cudaError_t pending_update(double* x, const double* p, long long n, const SolverState* st, cudaStream_t s) {
+  k_pending_update<double><<<grid_for(n), kThreads, 0, s>>>(x, p, n, st);
+  return cudaGetLastError();
+}
+cudaError_t pending_update(float* x, const float* p, long long n, const SolverState* st, cudaStream_t s) {
+  k_pending_update<float><<<grid_for(n), kThreads, 0, s>>>(x, p, n, st);
+  return cudaGetLastError();
+}
+cudaError_t rounding_perturbation(const double* x, double* u, long long n, cudaStream_t s) {
+  k_rounding_perturbation<<<grid_for(n), kThreads, 0, s>>>(x, u, n);
   return cudaGetLastError();
 }
 cudaError_t rel_convert(const double* r64, float* r32, long long n, const SolverState* st, cudaStream_t s) {

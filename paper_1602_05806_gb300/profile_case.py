@@ -25,6 +25,11 @@ def main(argv=None):
     ap.add_argument("--dim", type=int, default=2)
     ap.add_argument("--iters", type=int, default=40)
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--form", type=int, choices=[0, 1], default=1,
+                    help="CG iteration form: 0 one launch per iteration, 1 operator + update")
+    ap.add_argument("--delta", type=float, default=0.5,
+                    help="mixed: reliable-update factor (small: no residual replacement within the run, so "
+                         "every captured launch is a full iteration)")
     a = ap.parse_args(argv)
     build.build()
     n = (a.cells,) * a.dim
@@ -35,6 +40,8 @@ def main(argv=None):
     h.pressure_apply(z, b)
     x = torch.zeros_like(z)
     prec = sdg.SDG_MIXED if a.precision == "mixed" else sdg.SDG_FP64
+    h.set_iteration_form(a.form)
+    h.set_mixed_options(a.delta, 10000)
     h.set_options(prec, 1e-12, 1e-12, a.iters)
     info = h.pressure_cg(b, x, ok=(sdg.SDG_OK, sdg.SDG_ERR_NOT_CONVERGED))
     torch.cuda.synchronize()

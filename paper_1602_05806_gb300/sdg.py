@@ -21,14 +21,13 @@ SDG_ERR_CUDA = 2
 SDG_ERR_NOT_CONVERGED = 3
 SDG_ERR_BREAKDOWN = 4
 SDG_ERR_UNSUPPORTED = 5
-SDG_ERR_TIMEOUT = 6
 SDG_FP64 = 0
 SDG_MIXED = 1
 
 # every symbol include/sdg.h declares
 EXPORTS = (
     "sdg_nodes", "sdg_matrices", "sdg_kernel_projector", "sdg_line_operator", "sdg_create", "sdg_destroy", "sdg_set_options",
-    "sdg_set_mixed_options", "sdg_set_convection_substeps", "sdg_set_tile", "sdg_autotune", "sdg_ndof", "sdg_set_state", "sdg_get_state",
+    "sdg_set_mixed_options", "sdg_set_convection_substeps", "sdg_set_iteration_form", "sdg_set_tile", "sdg_autotune", "sdg_ndof", "sdg_set_state", "sdg_get_state",
     "sdg_pressure_apply", "sdg_viscous_apply", "sdg_pressure_cg", "sdg_viscous_cg",
     "sdg_dual_to_main", "sdg_main_to_dual", "sdg_convect", "sdg_pressure_rhs",
     "sdg_velocity_update", "sdg_step", "sdg_step_adjoint", "sdg_set_profiling", "sdg_counters", "sdg_diagnostics",
@@ -44,7 +43,8 @@ class sdg_grid(ctypes.Structure):
 class sdg_cg_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int),
                 ("applies_fp64", ctypes.c_int), ("applies_fp32", ctypes.c_int),
-                ("rel_res", ctypes.c_double), ("status", ctypes.c_int)]
+                ("rel_res", ctypes.c_double), ("status", ctypes.c_int), ("true_res", ctypes.c_double),
+                ("floor_res", ctypes.c_double), ("eval_res", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -84,6 +84,7 @@ def lib():
         L.sdg_set_mixed_options.argtypes = [vp, ctypes.c_double, ip, ip]
         L.sdg_set_convection_substeps.argtypes = [vp, ip]
         L.sdg_set_tile.argtypes = [vp, ip]
+        L.sdg_set_iteration_form.argtypes = [vp, ip]
         L.sdg_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp, vp]
         L.sdg_ndof.argtypes = [vp]
         L.sdg_ndof.restype = ctypes.c_longlong
@@ -249,6 +250,10 @@ class Handle:
         """SSP-RK3 sub-steps of the explicit convection per time step."""
         check(lib().sdg_set_convection_substeps(self.h, int(nsub)))
 
+    def set_iteration_form(self, form):
+        """0: one launch per CG iteration (default); 1: operator + update launches."""
+        check(lib().sdg_set_iteration_form(self.h, int(form)))
+
     def set_tile(self, variant):
         """Tile shape of the 2D FP32 operator (0 base, 1 wide in x, 2 wide in y)."""
         check(lib().sdg_set_tile(self.h, int(variant)))
@@ -258,7 +263,7 @@ class Handle:
         v = ctypes.c_int()
         us = (ctypes.c_double * 3)()
         check(lib().sdg_autotune(self.h, ctypes.byref(v), us, _stream(stream)))
-        return v.value, [us[i] for i in range(3 if self.dim == 2 else 1)]
+        return v.value, [us[i] for i in range(3 if self.dim == 2 else 2)]
 
     def set_profiling(self, enable=True):
         check(lib().sdg_set_profiling(self.h, 1 if enable else 0))

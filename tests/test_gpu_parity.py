@@ -6,7 +6,18 @@ Tolerances (relative L2 over the whole field unless stated):
     no cancellation);
   * FP32 operator apply: 2e-5 (3 n1 d terms in FP32, unit roundoff 6e-8);
   * pressure / velocity after each FP64 step: 1e-11; mixed-precision steps:
-    1e-10 (the accuracy the solvers are asked for).
+    1e-10, both against the oracle's step with both systems solved exactly.
+    One exception, pressure only: for odd N the pressure of a step is fixed
+    by FP64 only to its sensitivity to rounding-sized changes of the 1D
+    blocks, which move its near-kernel modes (tests/test_oracle_pins.py::
+    test_pressure_sensitivity_to_operator_rounding): about 4e-10 on the
+    256 x 256, N = 7 benchmark grid and a few 1e-11 on grids of about 10 x 10
+    cells, more for mixed solves, whose FP32 iterations resolve these modes
+    last; the bound for odd N is 1e-9 (1e-10 for the FP64 solves of small
+    grids).  The velocity, which sees only the gradient of q, keeps 1e-11
+    everywhere.
+The solves run to rtol 1e-14, which the solvers raise to three times the
+residual floor of FP64 vectors when that is larger (sdg_cg_info.floor_res).
 Grids are chosen to span several element tiles with ragged tails.
 """
 import math
@@ -50,7 +61,7 @@ APPLY_CASES = ([(2, (11, 7), N) for N in range(0, 12)]
                + [(2, (1, 5), 3), (2, (2, 2), 7), (2, (37, 3), 1)]
                + [(3, (5, 3, 4), N) for N in range(0, 7)]
                + [(3, (3, 2, 3), N) for N in range(7, 12)]
-               + [(3, (1, 2, 3), 4)])
+               + [(3, (1, 2, 3), 4), (3, (5, 6, 9), 4), (3, (9, 2, 11), 3)])
 
 
 @pytest.mark.parametrize("dim,n,N", APPLY_CASES)
@@ -133,11 +144,62 @@ def test_tile_variants_apply_and_mixed_cg(N):
         B, X = dev(b), dev(x0)
         info = h.pressure_cg(B, X)
         assert info["status"] == sdg.SDG_OK, (v, info)
-        # the mixed solver's stopping rule: true residual <= rtol, or <= 10 rtol
-        # once it stagnates at its FP64 floor
-        assert np.linalg.norm(b - o.pressure_apply(host(X))) <= 1e-12 * np.linalg.norm(b), v
+        # the stopping rule: true residual <= max(rtol, 3 floor), or <= 10 floor once it stalls
+        tol = max(1e-13, 10.0 * info["floor_res"])
+        assert info["true_res"] <= tol, (v, info)
+        assert np.linalg.norm(b - o.pressure_apply(host(X))) <= 1.5 * tol * np.linalg.norm(b), v
     best, us = h.autotune()
     assert best in (0, 1, 2) and len(us) == 3 and min(us) > 0.0
+
+
+@pytest.mark.parametrize("N", [1, 2, 4])
+def test_3d_kernels_agree(N):
+    """3D operator kernels: the z-marching column kernel (tile 0, default for
+    N <= 4) and the element-box kernel (tile 1) on a grid with ragged
+    columns and ragged runs of planes, plain applies in FP64 and FP32 against
+    the oracle, and a one-launch FP64 CG and a mixed CG with each."""
+    o, h = make(3, (6, 5, 9), N, L=(1.3, 2.1, 0.7))
+    rng = np.random.default_rng(60 + N)
+    x = rng.standard_normal(o.shape)
+    b = o.pressure_apply(rng.standard_normal(o.shape))
+    x0 = rng.standard_normal(o.shape)
+    ref = o.pressure_apply(x)
+    sols = []
+    for v in (0, 1):
+        h.set_tile(v)
+        X = dev(x)
+        Y = torch.empty_like(X)
+        h.pressure_apply(X, Y)
+        assert rel(host(Y), ref) <= 1e-13, v
+        Y32 = torch.empty_like(X.float())
+        h.pressure_apply(X.float(), Y32)
+        assert rel(host(Y32), o.pressure_apply(host(X.float()))) <= 2e-5, v
+        for prec in (sdg.SDG_FP64, sdg.SDG_MIXED):
+            h.set_options(prec, 1e-13, 1e-13, 1000000)
+            Xs = dev(x0)
+            info = h.pressure_cg(dev(b), Xs)
+            assert info["status"] == sdg.SDG_OK, (v, prec, info)
+            assert info["true_res"] <= max(1e-13, 10.0 * info["floor_res"]), (v, prec, info)
+            sols.append((prec, host(Xs)))
+    ex = o.pressure_solve_exact(b, x0)
+    for k, (prec, xs) in enumerate(sols):
+        assert rel(xs, ex) <= (1e-11 if prec == sdg.SDG_FP64 else 1e-10), k
+
+
+def test_full_size_apply_48cubed_N4():
+    """Every output of the 3D operator at the 48^3, N = 4 workload size
+    (13.8 M DOF), FP64 and FP32, z-marching kernel."""
+    o, h = make(3, (48, 48, 48), 4, nu=1.0 / 1600, theta=0.51, dt=1e-3)
+    x = si.random_vector(7, o.ndof).reshape(o.shape)
+    X = dev(x)
+    Y = torch.empty_like(X)
+    h.pressure_apply(X, Y)
+    ref = o.pressure_apply(x)
+    assert rel(host(Y), ref) <= 1e-13
+    X32 = X.float()
+    Y32 = torch.empty_like(X32)
+    h.pressure_apply(X32, Y32)
+    assert rel(host(Y32), o.pressure_apply(host(X32))) <= 2e-5
 
 
 def test_viscous_cg_fp64_and_mixed():
@@ -310,10 +372,9 @@ def test_step_parity_above_cfl_limit(precision):
     Eq. CFL1, run with five convection sub-steps per dt; four steps compared
     with the oracle after each."""
     o, h = make(2, (8, 8), 7, nu=1e-3, theta=0.51, dt=0.064)
-    o.rtol_p = o.rtol_v = 1e-13
     o.nsub = 5
     h.set_convection_substeps(5)
-    h.set_options(precision, 1e-13, 1e-13, 1000000)
+    h.set_options(precision, 1e-14, 1e-14, 1000000)
     modes = si.stream_modes(0, 32, 8, 1e-2)
     U, P = _oracle_tg(o, modes)
     Ug, Pg = taylor_green_state(2, (8, 8), (TWO_PI, TWO_PI), 7, modes=modes)
@@ -322,14 +383,14 @@ def test_step_parity_above_cfl_limit(precision):
     Uo = [torch.empty(o.shape, dtype=torch.float64, device="cuda") for _ in range(2)]
     Po = torch.empty(o.shape, dtype=torch.float64, device="cuda")
     for step in range(4):
-        U, P, _ = o.step(U, P)
+        U, P = o.step_exact(U, P)
         assert h.step(1)["status"] == sdg.SDG_OK
         h.get_state(Uo, Po)
         for d in range(2):
             e = rel(host(Uo[d]), U[d])
             assert e <= tol, (step, d, e)
         e = rel(host(Po), P)
-        assert e <= 1e-10, (step, e)
+        assert e <= tol, (step, e)
 
 
 def test_step_parity_perturbed_64x64_N5_reduced():
@@ -339,21 +400,19 @@ def test_step_parity_perturbed_64x64_N5_reduced():
     o, h = make(2, w["n"], w["N"], nu=w["nu"], theta=w["theta"], dt=w["dt"])
     o.nsub = w["nsub"]
     h.set_convection_substeps(w["nsub"])
-    o.rtol_p = o.rtol_v = 1e-13
-    h.set_options(sdg.SDG_FP64, 1e-13, 1e-13, 1000000)
+    h.set_options(sdg.SDG_FP64, 1e-14, 1e-14, 1000000)
     m = w["modes"]
     U, P = _oracle_tg(o, si.stream_modes(m["seed"], m["nmodes"], m["kmax"], m["amplitude"]))
     h.set_state([dev(u) for u in Ug], dev(Pg))
     Uo = [torch.empty(o.shape, dtype=torch.float64, device="cuda") for _ in range(2)]
     Po = torch.empty(o.shape, dtype=torch.float64, device="cuda")
     for _ in range(3):
-        U, P, _ = o.step(U, P)
+        U, P = o.step_exact(U, P)
         assert h.step(1)["status"] == sdg.SDG_OK
     h.get_state(Uo, Po)
     for d in range(2):
         assert rel(host(Uo[d]), U[d]) <= 1e-11
-    # two CGs stopped at rtol differ in P by up to about cond(A) * rtol; the
-    # velocity only sees the gradient of P and stays at 1e-11
+    # odd N: the pressure is fixed by FP64 only to its near-kernel sensitivity
     assert rel(host(Po), P) <= 1e-10
 
 
@@ -367,7 +426,7 @@ def test_step_parity_tg3d_N4_reduced(precision):
     o, h = make(3, w["n"], w["N"], nu=w["nu"], theta=w["theta"], dt=w["dt"])
     o.nsub = w["nsub"]
     h.set_convection_substeps(w["nsub"])
-    h.set_options(precision, 1e-13, 1e-13, 1000000)
+    h.set_options(precision, 1e-14, 1e-14, 1000000)
     U, P = _oracle_tg(o)
     h.set_state([dev(u) for u in Ug], dev(Pg))
     Uo = [torch.empty(o.shape, dtype=torch.float64, device="cuda") for _ in range(3)]
@@ -384,7 +443,7 @@ def test_step_parity_tg3d_N4_reduced(precision):
             e = float(np.linalg.norm(host(Uo[d]) - U[d])) / unorm
             assert e <= tol, (step, d, e)
         e = rel(host(Po), P)
-        assert e <= (1e-10 if precision == sdg.SDG_FP64 else 1e-8), (step, e)
+        assert e <= tol, (step, e)
         ke, _ = h.diagnostics()
         assert abs(ke - o.kinetic_energy(U)) <= 1e-12 * o.kinetic_energy(U)
 
@@ -406,12 +465,13 @@ def test_full_size_apply_256x256_N7():
 
 @pytest.mark.parametrize("precision", [sdg.SDG_FP64, sdg.SDG_MIXED])
 def test_full_size_step_256x256_N7(precision):
-    """One step of the benchmark workload (4.19 M DOF per field) against the
-    oracle's step with both linear systems solved exactly (block-circulant
-    Fourier solve, true residual ~1e-15).  The GPU solves stop at rtol 1e-12:
-    its velocity matches to 1e-11 and its pressure to 1e-9 (a CG stopped at
-    rtol 1e-12 on this system, cond ~1e7, carries pressure errors of order
-    1e-10 in its smoothest modes)."""
+    """One step of the benchmark workload (4.19 M DOF per field, rtol 1e-12 as
+    benchmarked) against the oracle's step with both linear systems solved
+    exactly.  Both solvers stop on the true FP64 residual, here at three
+    times its floor (about 3e-12: the residual that rounding the solution to
+    FP64 leaves).  The velocity matches to 1e-11; the pressure to 1e-9, the
+    precision to which FP64 fixes the pressure of this odd-N system (see the
+    module docstring)."""
     w, Ug, Pg = workload_state("tg2d_256x256_N7")
     assert w["nsub"] == 5  # CFL 2.47 by Eq. CFL1
     o, h = make(2, w["n"], w["N"], nu=w["nu"], theta=w["theta"], dt=w["dt"])
@@ -421,6 +481,9 @@ def test_full_size_step_256x256_N7(precision):
     h.set_state([dev(u) for u in Ug], dev(Pg))
     info = h.step(1)
     assert info["status"] == sdg.SDG_OK
+    pi = info["pressure"]
+    assert 1e-13 < pi["floor_res"] < 1e-11, pi
+    assert pi["true_res"] <= max(1e-12, 10.0 * pi["floor_res"]), pi
     Uo = [torch.empty(o.shape, dtype=torch.float64, device="cuda") for _ in range(2)]
     Po = torch.empty(o.shape, dtype=torch.float64, device="cuda")
     h.get_state(Uo, Po)
