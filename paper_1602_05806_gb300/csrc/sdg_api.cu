@@ -110,7 +110,10 @@ cudaError_t apply_plain(const sdg_handle* h, const Op& op, const T* x, T* y, cud
 // iteration like p: iteration j reads r[j&1], p[j&1], Ap[j&1] and writes the
 // other three, so after j iterations the current residual is r[j&1]);
 // otherwise the operator launch and the update launch of the two-launch form
-// (r[0], Ap[0]; the kernel deflation of the FP32 iteration runs there).
+// (r[0], Ap[0]; the kernel deflation of the FP32 iteration runs in the
+// update launch).  In the two-launch form the operator launch of iteration k
+// adds alpha_{k-1} p_{k-1} to x, so the update launch moves only r and Ap;
+// the last step's alpha p is added when the loop returns.
 // Convergence (and, in reliable mode, the need for an FP64 residual
 // replacement) is decided on the device; the host reads the state after each
 // batch of iterations.  Returns with h->st_host[sid] current.
@@ -160,20 +163,22 @@ int cg_loop(sdg_handle* h, const Op& op, T* x, T* const* r, T* const* p, T* cons
         a.y = Ap[j1];
         a.xsol = x;
       } else {
+        // the operator launch also adds the previous step alpha p to x
         a.fuse = 1;
         a.x = r[0];
         a.y = Ap[0];
+        a.xsol = x;
         a.kc = deflate ? h->kc : nullptr;
       }
       if (prof) SDG_CK(cudaEventRecord(h->pev[2 * k], s));
       if constexpr (sizeof(T) == 8) {
         SDG_K(launch_apply_f64(h, a, s));
         if (prof) SDG_CK(cudaEventRecord(h->pev[2 * k + 1], s));
-        if (!fused) SDG_K(cg_update_f64(x, r[0], p[j1], Ap[0], n, st, pa, s));
+        if (!fused) SDG_K(cg_update_f64(nullptr, r[0], nullptr, Ap[0], n, st, pa, s));
       } else {
         SDG_K(launch_apply_f32(h, a, s));
         if (prof) SDG_CK(cudaEventRecord(h->pev[2 * k + 1], s));
-        if (!fused) SDG_K(cg_update_f32(x, r[0], p[j1], Ap[0], n, st, pa, df, s));
+        if (!fused) SDG_K(cg_update_f32(nullptr, r[0], nullptr, Ap[0], n, st, pa, df, s));
       }
       ++launched;
     }
@@ -199,6 +204,12 @@ int cg_loop(sdg_handle* h, const Op& op, T* x, T* const* r, T* const* p, T* cons
     }
     if (segment_cap > 0 && hs.iter - iter_start >= segment_cap) break;  // caller replaces the residual
     if (batch < 32) batch *= 2;
+  }
+  if (!fused) {
+    // the last operator launch (iteration iter - 1) wrote p[iter & 1]; its
+    // alpha p is still to be added to x (no-op after a breakdown: alpha 0)
+    SDG_K(pending_x(x, p[h->st_host[sid].iter & 1], n, st, s));
+    h->st_host[sid].xpend = 0;
   }
   return SDG_OK;
 }

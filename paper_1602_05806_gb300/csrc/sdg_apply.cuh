@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(Tile<DIM, N1, TV>::THREADS, (apply_min_blocks<
   }
 
   pdl_wait();
-  bool first = false;
+  bool first = false, xupd = false;
   T beta = T(0), alpha = T(0);
   if (fuse) {
     if (a.st->done || a.st->pause) return;  // uniform: written by the previous kernel
@@ -405,6 +405,8 @@ __global__ void __launch_bounds__(Tile<DIM, N1, TV>::THREADS, (apply_min_blocks<
     if (!first) {
       beta = sizeof(T) == 4 ? (T)a.st->beta_f : (T)a.st->beta;
       alpha = sizeof(T) == 4 ? (T)a.st->alpha_f : (T)a.st->alpha;
+      // two-launch form: x += alpha_{k-1} p_{k-1} on the owned nodes
+      xupd = !fuse2 && a.xsol != nullptr && a.st->xpend != 0;
     }
   }
   if (defl)
@@ -499,6 +501,13 @@ __global__ void __launch_bounds__(Tile<DIM, N1, TV>::THREADS, (apply_min_blocks<
         T* vp = reinterpret_cast<T*>(&val);
 #pragma unroll
         for (int k = 0; k < VW; ++k) vp[k] = rp[k] + beta * pp[k];
+        if (xupd && s < TE) {
+          V xv = reinterpret_cast<const V*>(a.xsol)[gi];
+          T* xp = reinterpret_cast<T*>(&xv);
+#pragma unroll
+          for (int k = 0; k < VW; ++k) xp[k] = fma(alpha, pp[k], xp[k]);
+          reinterpret_cast<V*>(a.xsol)[gi] = xv;
+        }
       }
       if (s < TE) reinterpret_cast<V*>(a.p_out)[gi] = val;
     }
@@ -668,6 +677,7 @@ __global__ void __launch_bounds__(Tile<DIM, N1, TV>::THREADS, (apply_min_blocks<
           st->alpha = st->rr / pAp;
         }
         st->alpha_f = (float)st->alpha;
+        if (a.xsol != nullptr) st->xpend = 1;  // x lacks alpha_k p_k
       }
     }
   }

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(March3<N1>::THREADS, (march3_min_blocks<T, ONE
   T* xhalo = ring + 3 * PE * ES;             // x = -1, x = VX faces: 2 TY * HS
   T* yhalo = xhalo + 2 * TY * HS;            // y = -1, y = VY faces (rows): 2 TX * ES
   T* s_out = yhalo + 2 * TX * ES;            // one accumulator per direction: 3 * PE * ES
-  T* rring = s_out + 3 * PE * ES;            // ONE: r_k of two owned planes, 2 * PE * ES
+  T* rring = s_out + 3 * PE * ES;            // ONE: r_k of the owned planes by ring slot, 3 * PE * ES
   __shared__ T s_w[N1];
 
   const bool fuse = ONE || a.fuse != 0;
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(March3<N1>::THREADS, (march3_min_blocks<T, ONE
   if (threadIdx.x < N1) s_w[threadIdx.x] = a.w[threadIdx.x];
 
   pdl_wait();
-  bool first = false;
+  bool first = false, xupd = false;
   T beta = T(0), alpha = T(0);
   if (fuse) {
     if (a.st->done || a.st->pause) return;  // uniform: written by the previous kernel
@@ -100,6 +100,8 @@ __global__ void __launch_bounds__(March3<N1>::THREADS, (march3_min_blocks<T, ONE
     if (!first) {
       beta = sizeof(T) == 4 ? (T)a.st->beta_f : (T)a.st->beta;
       alpha = sizeof(T) == 4 ? (T)a.st->alpha_f : (T)a.st->alpha;
+      // two-launch form: x += alpha_{k-1} p_{k-1} on the owned nodes
+      xupd = !ONE && a.xsol != nullptr && a.st->xpend != 0;
     }
   }
 
@@ -128,8 +130,16 @@ __global__ void __launch_bounds__(March3<N1>::THREADS, (march3_min_blocks<T, ONE
       }
       return r;
     } else {
-      const T p = first ? r : fma(beta, a.p_old[gi], r);
-      if (owned) a.p_out[gi] = p;
+      if (first) {
+        if (owned) a.p_out[gi] = r;
+        return r;
+      }
+      const T po = a.p_old[gi];
+      const T p = fma(beta, po, r);
+      if (owned) {
+        a.p_out[gi] = p;
+        if (xupd) a.xsol[gi] = fma(alpha, po, a.xsol[gi]);
+      }
       return p;
     }
   };
@@ -142,7 +152,9 @@ __global__ void __launch_bounds__(March3<N1>::THREADS, (march3_min_blocks<T, ONE
   // start on 16-byte boundaries, and box planes, y-face halo and stores move
   // as float4 / double2 with one index computation per vector.
   constexpr int RV = TX * NPE / VW;  // vectors per row
-  const bool vec = (RS == N1) && (TX * NPE) % VW == 0 && VX == TX && nx % VW == 0;
+  const size_t plane = (size_t)nx * ny * NPE;
+  // (offsets within a plane are 32-bit in the vector path)
+  const bool vec = (RS == N1) && (TX * NPE) % VW == 0 && VX == TX && nx % VW == 0 && plane < (size_t(1) << 31);
   // x-face halo elements in the vector path: element ox - 1 ends and element
   // ox + VX starts on a vector boundary (both neighbour a full, aligned row
   // of the column, or wrap to a row end / start), so each moves as the HS / VW
@@ -150,7 +162,6 @@ __global__ void __launch_bounds__(March3<N1>::THREADS, (march3_min_blocks<T, ONE
   // sits LOFF values into its slot, the few values before it are unused
   constexpr int LOFF = (VW - NPE % VW) % VW;
   const int loff = vec ? LOFF : 0;
-  const size_t plane = (size_t)nx * ny * NPE;
   // stage() on the VW values of one vector
   auto stage_vec = [&](size_t gi, bool owned, VT* rk) -> VT {
     VT out, rv;
@@ -195,6 +206,13 @@ __global__ void __launch_bounds__(March3<N1>::THREADS, (march3_min_blocks<T, ONE
         const T* pp = reinterpret_cast<const T*>(&po);
 #pragma unroll
         for (int k = 0; k < VW; ++k) o[k] = fma(beta, pp[k], rp[k]);
+        if (owned && xupd) {
+          VT xv = *reinterpret_cast<const VT*>(a.xsol + gi);
+          T* xp = reinterpret_cast<T*>(&xv);
+#pragma unroll
+          for (int k = 0; k < VW; ++k) xp[k] = fma(alpha, pp[k], xp[k]);
+          *reinterpret_cast<VT*>(a.xsol + gi) = xv;
+        }
       }
       if (owned) *reinterpret_cast<VT*>(a.p_out + gi) = out;
       (void)rr;
@@ -202,21 +220,72 @@ __global__ void __launch_bounds__(March3<N1>::THREADS, (march3_min_blocks<T, ONE
     }
   };
 
+  // Per-thread vectors of the vector path, fixed over the march: box rows
+  // (boff: offset in a plane of the global arrays, bsi: in a ring slot), the
+  // y-face rows (yoff, ysi) and the x-face elements (xoff, xsi); -1 = none.
+  constexpr int HV = HS / VW;                                  // vectors per x-face element
+  constexpr int NBV = (PE * NPE) / VW;                         // box vectors of a plane
+  constexpr int KP = (NBV + THREADS - 1) / THREADS;
+  constexpr int KY = (2 * RV + THREADS - 1) / THREADS;
+  constexpr int KX = (2 * TY * HV + THREADS - 1) / THREADS;
+  int boff[KP], bsi[KP], yoff[KY], ysi[KY], xoff[KX], xsi[KX];
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    const int v = threadIdx.x + k * THREADS;
+    boff[k] = -1;
+    bsi[k] = 0;
+    if (vec && v < VY * RV) {
+      const int row = v / RV, i = v - row * RV;
+      boff[k] = ((oy + row) * nx + ox) * NPE + i * VW;
+      bsi[k] = row * TX * ES + i * VW;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < KY; ++k) {
+    const int v = threadIdx.x + k * THREADS;
+    yoff[k] = -1;
+    ysi[k] = 0;
+    if (vec && v < 2 * RV) {
+      const int side = v / RV, i = v - side * RV;
+      int gy = side ? oy + VY : oy - 1;
+      gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
+      yoff[k] = (gy * nx + ox) * NPE + i * VW;
+      ysi[k] = side * TX * ES + i * VW;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < KX; ++k) {
+    const int v = threadIdx.x + k * THREADS;
+    xoff[k] = -1;
+    xsi[k] = 0;
+    if (vec && v < 2 * TY * HV) {
+      const int s = v / HV, j = v - s * HV;
+      const int sy = s < TY ? s : s - TY;
+      if (sy < VY) {
+        int gx = s < TY ? ox - 1 : ox + VX;
+        gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
+        const int ge = (oy + sy) * nx + gx;
+        xoff[k] = (s < TY ? (ge + 1) * NPE - HS : ge * NPE) + j * VW;
+        xsi[k] = s * HS + j * VW;
+      }
+    }
+  }
+
   // box of plane iz (relative to z0) into its ring slot; owned iff 0 <= iz < NZ
   auto load_plane = [&](int iz) {
     const int z = wrapz(z0 + iz);
     const bool owned = iz >= 0 && iz < NZ;
     T* dst = ring + ring_slot(iz) * PE * ES;
-    T* rdst = rring + (iz & 1) * PE * ES;
+    T* rdst = rring + ring_slot(iz) * PE * ES;
     if (vec) {
-      for (int v = threadIdx.x; v < VY * RV; v += THREADS) {
-        const int row = v / RV, i = v - row * RV;
-        const size_t gi = (size_t)z * plane + ((size_t)(oy + row) * nx + ox) * NPE + (size_t)i * VW;
-        const int si = row * TX * ES + i * VW;
+      const size_t zb = (size_t)z * plane;
+#pragma unroll
+      for (int k = 0; k < KP; ++k) {
+        if (boff[k] < 0) continue;
         VT rk;
-        *reinterpret_cast<VT*>(dst + si) = stage_vec(gi, owned, &rk);
+        *reinterpret_cast<VT*>(dst + bsi[k]) = stage_vec(zb + boff[k], owned, &rk);
         if constexpr (ONE) {
-          if (owned) *reinterpret_cast<VT*>(rdst + si) = rk;
+          if (owned) *reinterpret_cast<VT*>(rdst + bsi[k]) = rk;
         }
       }
       return;
@@ -239,28 +308,14 @@ __global__ void __launch_bounds__(March3<N1>::THREADS, (march3_min_blocks<T, ONE
   auto load_halo = [&](int iz) {
     const int z = wrapz(z0 + iz);
     if (vec) {
-      // y = -1 and y = VY rows as vectors
-      for (int v = threadIdx.x; v < 2 * RV; v += THREADS) {
-        const int side = v / RV, i = v - side * RV;
-        int gy = side ? oy + VY : oy - 1;
-        gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
-        const size_t gi = (size_t)z * plane + ((size_t)gy * nx + ox) * NPE + (size_t)i * VW;
-        VT rk;
-        *reinterpret_cast<VT*>(yhalo + side * TX * ES + i * VW) = stage_vec(gi, false, &rk);
-      }
-      // x = -1 and x = VX elements as the aligned vectors around them
-      constexpr int HV = HS / VW;
-      for (int v = threadIdx.x; v < 2 * TY * HV; v += THREADS) {
-        const int s = v / HV, j = v - s * HV;
-        const int sy = s < TY ? s : s - TY;
-        if (sy >= VY) continue;
-        int gx = s < TY ? ox - 1 : ox + VX;
-        gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
-        const size_t ge = ((size_t)z * ny + (oy + sy)) * nx + gx;
-        const size_t g0 = s < TY ? (ge + 1) * NPE - HS : ge * NPE;
-        VT rk;
-        *reinterpret_cast<VT*>(xhalo + s * HS + j * VW) = stage_vec(g0 + (size_t)j * VW, false, &rk);
-      }
+      const size_t zb = (size_t)z * plane;
+      VT rk;
+#pragma unroll
+      for (int k = 0; k < KY; ++k)
+        if (yoff[k] >= 0) *reinterpret_cast<VT*>(yhalo + ysi[k]) = stage_vec(zb + yoff[k], false, &rk);
+#pragma unroll
+      for (int k = 0; k < KX; ++k)
+        if (xoff[k] >= 0) *reinterpret_cast<VT*>(xhalo + xsi[k]) = stage_vec(zb + xoff[k], false, &rk);
       return;
     }
     for (int v = threadIdx.x; v < HALO * NPE; v += THREADS) {
@@ -288,6 +343,66 @@ __global__ void __launch_bounds__(March3<N1>::THREADS, (march3_min_blocks<T, ONE
     }
   };
 
+  // reductions: p.Ap (fuse 1, compensated); ONE: p.Ap, r.r (compensated), r.Ap, Ap.Ap
+  T s_pa = T(0), c_pa = T(0), s_rr = T(0), c_rr = T(0), s_ra = T(0), s_aa = T(0);
+  auto reduce = [&](T y, T pv, T r) {
+    const T t1 = fma(pv, y, -c_pa);
+    const T u1 = s_pa + t1;
+    c_pa = (u1 - s_pa) - t1;
+    s_pa = u1;
+    if constexpr (ONE) {
+      const T t2 = fma(r, r, -c_rr);
+      const T u2 = s_rr + t2;
+      c_rr = (u2 - s_rr) - t2;
+      s_rr = u2;
+      s_ra = fma(r, y, s_ra);
+      s_aa = fma(y, y, s_aa);
+    }
+  };
+  // y = sum of the three direction accumulators of plane iz, stored; reduced in CG modes
+  auto store_plane = [&](int iz) {
+    const int z = z0 + iz;
+    const T* cur = ring + ring_slot(iz) * PE * ES;
+    const T* rk = rring + ring_slot(iz) * PE * ES;
+    if (vec) {
+      const size_t zb = (size_t)z * plane;
+#pragma unroll
+      for (int k = 0; k < KP; ++k) {
+        if (boff[k] < 0) continue;
+        const int si = bsi[k];
+        VT yv = *reinterpret_cast<const VT*>(s_out + si);
+        const VT y1 = *reinterpret_cast<const VT*>(s_out + PE * ES + si);
+        const VT y2 = *reinterpret_cast<const VT*>(s_out + 2 * PE * ES + si);
+        T* yw = reinterpret_cast<T*>(&yv);
+        const T* a1 = reinterpret_cast<const T*>(&y1);
+        const T* a2 = reinterpret_cast<const T*>(&y2);
+#pragma unroll
+        for (int m = 0; m < VW; ++m) yw[m] = (yw[m] + a1[m]) + a2[m];
+        *reinterpret_cast<VT*>(a.y + zb + boff[k]) = yv;
+        if (fuse) {
+          const VT pv4 = *reinterpret_cast<const VT*>(cur + si);
+          const T* pp = reinterpret_cast<const T*>(&pv4);
+          VT rv4;
+          if constexpr (ONE) rv4 = *reinterpret_cast<const VT*>(rk + si);
+          const T* rp = reinterpret_cast<const T*>(&rv4);
+#pragma unroll
+          for (int m = 0; m < VW; ++m) reduce(yw[m], pp[m], ONE ? rp[m] : T(0));
+        }
+      }
+      return;
+    }
+    for (int v = threadIdx.x; v < PE * NPE; v += THREADS) {
+      const int s = v / NPE, q = v - s * NPE;
+      const int sx = s % TX, sy = s / TX;
+      if (sx >= VX || sy >= VY) continue;
+      const long long ge = ((long long)z * ny + (oy + sy)) * nx + (ox + sx);
+      const int si = s * ES + m3_sidx<N1>(q);
+      const T y = (s_out[si] + s_out[PE * ES + si]) + s_out[2 * PE * ES + si];
+      a.y[(size_t)ge * NPE + q] = y;
+      if (fuse) reduce(y, cur[si], ONE ? rk[si] : T(0));
+    }
+  };
+
   // this thread's line in each direction
   const int t = threadIdx.x;
   const int te = t / LINES, lam = t - te * LINES;
@@ -295,15 +410,16 @@ __global__ void __launch_bounds__(March3<N1>::THREADS, (march3_min_blocks<T, ONE
   const bool active = lx < VX && ly < VY;
   const int q0 = lam % N1, q1 = lam / N1;
 
-  // reductions: p.Ap (fuse 1, compensated); ONE: p.Ap, r.r (compensated), r.Ap, Ap.Ap
-  T s_pa = T(0), c_pa = T(0), s_rr = T(0), c_rr = T(0), s_ra = T(0), s_aa = T(0);
-
+  // March: planes iz - 1, iz, iz + 1 are in the ring when plane iz is
+  // computed.  Two barriers per plane: after the passes, and after storing
+  // plane iz while loading plane iz + 2 (into the slot of iz - 1) and the
+  // halo of iz + 1.
   load_plane(-1);
   load_plane(0);
+  load_plane(1);
+  load_halo(0);
+  __syncthreads();
   for (int iz = 0; iz < NZ; ++iz) {
-    load_plane(iz + 1);
-    load_halo(iz);
-    __syncthreads();
     const T* cur = ring + ring_slot(iz) * PE * ES;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -350,78 +466,12 @@ __global__ void __launch_bounds__(March3<N1>::THREADS, (march3_min_blocks<T, ONE
       }
     }
     __syncthreads();
-    // store the plane (owned) and reduce
-    const int z = z0 + iz;
-    const T* rk = rring + (iz & 1) * PE * ES;
-    if (vec) {
-      for (int v = threadIdx.x; v < VY * RV; v += THREADS) {
-        const int row = v / RV, i = v - row * RV;
-        const size_t gi = (size_t)z * plane + ((size_t)(oy + row) * nx + ox) * NPE + (size_t)i * VW;
-        const int si = row * TX * ES + i * VW;
-        VT yv = *reinterpret_cast<const VT*>(s_out + si);
-        {
-          const VT y1 = *reinterpret_cast<const VT*>(s_out + PE * ES + si);
-          const VT y2 = *reinterpret_cast<const VT*>(s_out + 2 * PE * ES + si);
-          T* yw = reinterpret_cast<T*>(&yv);
-          const T* a1 = reinterpret_cast<const T*>(&y1);
-          const T* a2 = reinterpret_cast<const T*>(&y2);
-#pragma unroll
-          for (int k = 0; k < VW; ++k) yw[k] = (yw[k] + a1[k]) + a2[k];
-        }
-        *reinterpret_cast<VT*>(a.y + gi) = yv;
-        if (fuse) {
-          const VT pv4 = *reinterpret_cast<const VT*>(cur + si);
-          const T* yp = reinterpret_cast<const T*>(&yv);
-          const T* pp = reinterpret_cast<const T*>(&pv4);
-#pragma unroll
-          for (int k = 0; k < VW; ++k) {
-            const T t1 = fma(pp[k], yp[k], -c_pa);
-            const T u1 = s_pa + t1;
-            c_pa = (u1 - s_pa) - t1;
-            s_pa = u1;
-          }
-          if constexpr (ONE) {
-            const VT rv4 = *reinterpret_cast<const VT*>(rk + si);
-            const T* rp = reinterpret_cast<const T*>(&rv4);
-#pragma unroll
-            for (int k = 0; k < VW; ++k) {
-              const T t2 = fma(rp[k], rp[k], -c_rr);
-              const T u2 = s_rr + t2;
-              c_rr = (u2 - s_rr) - t2;
-              s_rr = u2;
-              s_ra = fma(rp[k], yp[k], s_ra);
-              s_aa = fma(yp[k], yp[k], s_aa);
-            }
-          }
-        }
-      }
-    } else
-    for (int v = threadIdx.x; v < PE * NPE; v += THREADS) {
-      const int s = v / NPE, q = v - s * NPE;
-      const int sx = s % TX, sy = s / TX;
-      if (sx >= VX || sy >= VY) continue;
-      const long long ge = ((long long)z * ny + (oy + sy)) * nx + (ox + sx);
-      const int si = s * ES + m3_sidx<N1>(q);
-      const T y = (s_out[si] + s_out[PE * ES + si]) + s_out[2 * PE * ES + si];
-      a.y[(size_t)ge * NPE + q] = y;
-      if (fuse) {
-        const T pv = cur[si];
-        const T t1 = fma(pv, y, -c_pa);
-        const T u1 = s_pa + t1;
-        c_pa = (u1 - s_pa) - t1;
-        s_pa = u1;
-        if constexpr (ONE) {
-          const T r = rk[si];
-          const T t2 = fma(r, r, -c_rr);
-          const T u2 = s_rr + t2;
-          c_rr = (u2 - s_rr) - t2;
-          s_rr = u2;
-          s_ra = fma(r, y, s_ra);
-          s_aa = fma(y, y, s_aa);
-        }
-      }
+    store_plane(iz);
+    if (iz + 1 < NZ) {  // uniform over the CTA
+      load_plane(iz + 2);
+      load_halo(iz + 1);
+      __syncthreads();
     }
-    __syncthreads();  // the next step overwrites the ring slot of plane iz - 1 and the halo
   }
 
   if (!fuse) return;
@@ -459,6 +509,7 @@ __global__ void __launch_bounds__(March3<N1>::THREADS, (march3_min_blocks<T, ONE
         st->alpha = st->rr / pAp;
       }
       st->alpha_f = (float)st->alpha;
+      if (a.xsol != nullptr) st->xpend = 1;  // x lacks alpha_k p_k
     }
   }
 }
@@ -480,7 +531,7 @@ cudaError_t launch_apply3m(const sdg_handle* h, const ApplyArgs<T>& in, cudaStre
   using M = March3<N1>;
   ApplyParams<T, 3, N1> p;
   fill_apply_params<T, 3, N1>(h, in, &p);
-  const size_t smem = ((size_t)((3 + 3) * M::PE + 2 * M::TX + (ONE ? 2 * M::PE : 0)) * M::ES +
+  const size_t smem = ((size_t)((3 + 3) * M::PE + 2 * M::TX + (ONE ? 3 * M::PE : 0)) * M::ES +
                        (size_t)2 * M::TY * m3_halo_slot<T, N1>()) * sizeof(T);
   // resident CTAs per SM of this instantiation (fixed: threads and shared
   // memory do not depend on the grid), measured once

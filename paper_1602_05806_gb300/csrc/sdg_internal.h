@@ -35,6 +35,8 @@ struct SolverState {
   int reliable;     // 1: FP32 iterations pause for FP64 residual replacement
   int pause;        // set by the update kernel when a reliable update is due
   int updates;      // reliable updates done
+  int xpend;        // two-launch form: 1 while x lacks alpha p of the last operator launch
+                    // (the next operator launch adds it, or the CG loop when it returns)
   unsigned int counter;  // last-block ticket counter (reset by the last block)
 };
 
@@ -160,6 +162,9 @@ struct ApplyArgs {
   const T* x;      // input (fuse = 0) or r (fuse = 1)
   const T* p_old;  // fuse = 1
   T* p_out;        // fuse = 1
+  // fuse = 1 with xsol set: the operator launch of iteration k also adds
+  // alpha_{k-1} p_{k-1} to xsol (state flag xpend), so that the update launch
+  // reads and writes only r and Ap
   T* y;
   double s[3];
   double cmass;
@@ -190,6 +195,7 @@ cudaError_t apply_dispatch_3d(const sdg_handle* h, const ApplyArgs<double>& a, c
 cudaError_t apply_dispatch_3d(const sdg_handle* h, const ApplyArgs<float>& a, cudaStream_t s);
 
 // ---- vector / step kernels (sdg_kernels.cu) --------------------------------
+// (x may be null: x += alpha p is then left to the next operator launch)
 cudaError_t cg_update_f64(double* x, double* r, const double* p, const double* Ap, long long n,
                           SolverState* st, double* partials, cudaStream_t s);
 cudaError_t cg_update_f32(float* x, float* r, const float* p, const float* Ap, long long n,
@@ -227,6 +233,10 @@ cudaError_t rel_renorm(const double* r, long long n, SolverState* st, double* pa
 // iteration stopped at maxit
 cudaError_t pending_update(double* x, const double* p, long long n, const SolverState* st, cudaStream_t s);
 cudaError_t pending_update(float* x, const float* p, long long n, const SolverState* st, cudaStream_t s);
+// x += alpha p if the state's xpend is set (the two-launch form's last step
+// when its CG loop returns), then xpend = 0
+cudaError_t pending_x(double* x, const double* p, long long n, SolverState* st, cudaStream_t s);
+cudaError_t pending_x(float* x, const float* p, long long n, SolverState* st, cudaStream_t s);
 
 // Restore the component of x in the kernel of the periodic pressure operator
 // to that of x0: c = (1/ncell) (P1 (x) ... (x) P1) sum_e (x - x0)[e], then

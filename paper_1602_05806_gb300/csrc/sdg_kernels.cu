@@ -86,7 +86,8 @@ __device__ __forceinline__ void upd1(T& x, T& r, T p, T Ap, T alpha, DotAcc<T>& 
   rr.add(r * r);
 }
 
-// x += alpha p ; r -= alpha Ap ; rr = r.r  (vectorised, scalar tail).
+// x += alpha p ; r -= alpha Ap ; rr = r.r  (vectorised, scalar tail).  With
+// x null only r and Ap move (the operator launch adds alpha p to x).
 // With deflation (FP32, df.kpart != null) the kernel part of the new r is
 // reduced too, removed from rr, and left in df.kc for the next direction.
 template <typename T>
@@ -113,15 +114,18 @@ __global__ void __launch_bounds__(kThreads)
   // U vectors per thread and pass, all loads issued before the arithmetic
   // (the update is bound by memory latency, not bandwidth, at one vector)
   constexpr int U = 2;
+  const bool withx = x != nullptr;
   for (long long i0 = tid; i0 < nv; i0 += U * nth) {
     V xv[U], rv[U], pv[U], av[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const long long i = i0 + u * nth;
       if (i < nv) {
-        xv[u] = reinterpret_cast<V*>(x)[i];
+        if (withx) {
+          xv[u] = reinterpret_cast<V*>(x)[i];
+          pv[u] = reinterpret_cast<const V*>(p)[i];
+        }
         rv[u] = reinterpret_cast<V*>(r)[i];
-        pv[u] = reinterpret_cast<const V*>(p)[i];
         av[u] = reinterpret_cast<const V*>(Ap)[i];
       }
     }
@@ -133,9 +137,17 @@ __global__ void __launch_bounds__(kThreads)
       T* rs = reinterpret_cast<T*>(&rv[u]);
       const T* ps = reinterpret_cast<const T*>(&pv[u]);
       const T* as = reinterpret_cast<const T*>(&av[u]);
+      if (withx) {
 #pragma unroll
-      for (int k = 0; k < W; ++k) upd1(xs[k], rs[k], ps[k], as[k], alpha, rr);
-      reinterpret_cast<V*>(x)[i] = xv[u];
+        for (int k = 0; k < W; ++k) upd1(xs[k], rs[k], ps[k], as[k], alpha, rr);
+        reinterpret_cast<V*>(x)[i] = xv[u];
+      } else {
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          rs[k] = fma(-alpha, as[k], rs[k]);
+          rr.add(rs[k] * rs[k]);
+        }
+      }
       reinterpret_cast<V*>(r)[i] = rv[u];
       if (defl) {
         const unsigned l0 = (unsigned)((unsigned long long)(i * W) % (unsigned)df.npe);
@@ -149,7 +161,12 @@ __global__ void __launch_bounds__(kThreads)
     }
   }
   for (long long i = nv * W + tid; i < n; i += nth) {
-    upd1(x[i], r[i], p[i], Ap[i], alpha, rr);
+    if (withx) {
+      upd1(x[i], r[i], p[i], Ap[i], alpha, rr);
+    } else {
+      r[i] = fma(-alpha, Ap[i], r[i]);
+      rr.add(r[i] * r[i]);
+    }
     if (defl) atomicAdd(&s_k[(unsigned)((unsigned long long)i % (unsigned)df.npe)], (float)r[i]);
   }
   if (defl) {
@@ -288,6 +305,7 @@ __global__ void __launch_bounds__(kThreads)
       st->status = SDG_OK;
       st->alpha = 0.0;
       st->pAp = 0.0;
+      st->xpend = 0;
     } else {
       st->updates += 1;
     }
@@ -385,6 +403,19 @@ __global__ void __launch_bounds__(kThreads)
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_pending_update(T* __restrict__ x, const T* __restrict__ p, long long n, const SolverState* st) {
+  const T alpha = sizeof(T) == 4 ? (T)st->alpha_f : (T)st->alpha;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = fma(alpha, p[i], x[i]);
+}
+
+// x += alpha p when the state's xpend is set (the step the next operator
+// launch of the two-launch form would have added); the flag is cleared by a
+// separate copy after this kernel
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_pending_x(T* __restrict__ x, const T* __restrict__ p, long long n, const SolverState* st) {
+  if (!st->xpend) return;
   const T alpha = sizeof(T) == 4 ? (T)st->alpha_f : (T)st->alpha;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
@@ -830,6 +861,20 @@ cudaError_t pending_update(double* x, const double* p, long long n, const Solver
 cudaError_t pending_update(float* x, const float* p, long long n, const SolverState* st, cudaStream_t s) {
   k_pending_update<float><<<grid_for(n), kThreads, 0, s>>>(x, p, n, st);
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t pending_x_t(T* x, const T* p, long long n, SolverState* st, cudaStream_t s) {
+  k_pending_x<T><<<grid_for(n), kThreads, 0, s>>>(x, p, n, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(&st->xpend, 0, sizeof(int), s);
+}
+cudaError_t pending_x(double* x, const double* p, long long n, SolverState* st, cudaStream_t s) {
+  return pending_x_t(x, p, n, st, s);
+}
+cudaError_t pending_x(float* x, const float* p, long long n, SolverState* st, cudaStream_t s) {
+  return pending_x_t(x, p, n, st, s);
 }
 cudaError_t rounding_perturbation(const double* x, double* u, long long n, cudaStream_t s) {
   k_rounding_perturbation<<<grid_for(n), kThreads, 0, s>>>(x, u, n);

@@ -152,13 +152,18 @@ def test_tile_variants_apply_and_mixed_cg(N):
     assert best in (0, 1, 2) and len(us) == 3 and min(us) > 0.0
 
 
-@pytest.mark.parametrize("N", [1, 2, 4])
-def test_3d_kernels_agree(N):
+@pytest.mark.parametrize("n,N", [((6, 5, 9), 1), ((6, 5, 9), 2), ((6, 5, 9), 4),
+                                 ((8, 6, 7), 0), ((8, 6, 7), 2), ((8, 6, 7), 4)])
+def test_3d_kernels_agree(n, N):
     """3D operator kernels: the z-marching column kernel (tile 0, default for
-    N <= 4) and the element-box kernel (tile 1) on a grid with ragged
-    columns and ragged runs of planes, plain applies in FP64 and FP32 against
-    the oracle, and a one-launch FP64 CG and a mixed CG with each."""
-    o, h = make(3, (6, 5, 9), N, L=(1.3, 2.1, 0.7))
+    N <= 4) and the element-box kernel (tile 1), plain applies in FP64 and
+    FP32 against the oracle, and an FP64 CG and a mixed CG with each.  The
+    6 x 5 x 9 grid has ragged columns and ragged runs of planes; on the
+    8 x 6 x 7 grid every column is full and nx is a multiple of the vector
+    width, so the marching kernel moves rows and x-face elements as aligned
+    vectors (odd N + 1: unpadded rows), with the x = -1 element offset in its
+    slot."""
+    o, h = make(3, n, N, L=(1.3, 2.1, 0.7))
     rng = np.random.default_rng(60 + N)
     x = rng.standard_normal(o.shape)
     b = o.pressure_apply(rng.standard_normal(o.shape))
