@@ -199,13 +199,13 @@ int sdg_set_convection_substeps(sdg_handle* h, int nsub);
  * the operator kernel of iteration k also applies the update of iteration
  * k-1 (r -= alpha Ap, x += alpha p) while it stages its input, and reduces
  * p.Ap, r.r, r.Ap and Ap.Ap, from which beta is formed one iteration ahead.
- * 1 (default): two launches per iteration, the operator (p = r + beta p,
- * Ap, p.Ap) and the update (x, r, r.r); measured faster (256 x 256, N = 7,
- * FP32: 50.5 against 53.8 us per iteration; a mixed step of that workload
- * 1.44 against 1.54 s).  Both are the CG of Sec. 2.1
- * in exact arithmetic; the FP32 kernel deflation of sdg_set_mixed_options
- * always uses the two-launch form.
- * Errors: INVALID_ARG unless form is 0 or 1. */
+ * 1: two launches per iteration, the operator (p = r + beta p, Ap, p.Ap)
+ * and the update (x += alpha p, r -= alpha Ap, r.r).  2 (default): two
+ * launches, with x += alpha p moved into the next operator launch (which
+ * reads p already), so that the update moves only r and Ap.  All are the CG
+ * of Sec. 2.1 in exact arithmetic; the FP32 kernel deflation of
+ * sdg_set_mixed_options always uses form 1.
+ * Errors: INVALID_ARG unless form is 0, 1 or 2. */
 int sdg_set_iteration_form(sdg_handle* h, int form);
 
 /* Tile shape of the operator kernel.  2D FP32 (a CTA's box of elements):

@@ -109,11 +109,12 @@ cudaError_t apply_plain(const sdg_handle* h, const Op& op, const T* x, T* y, cud
 // fused: one launch per iteration (r[2] and Ap[2] alternate with the
 // iteration like p: iteration j reads r[j&1], p[j&1], Ap[j&1] and writes the
 // other three, so after j iterations the current residual is r[j&1]);
-// otherwise the operator launch and the update launch of the two-launch form
+// otherwise the operator launch and the update launch of a two-launch form
 // (r[0], Ap[0]; the kernel deflation of the FP32 iteration runs in the
-// update launch).  In the two-launch form the operator launch of iteration k
-// adds alpha_{k-1} p_{k-1} to x, so the update launch moves only r and Ap;
-// the last step's alpha p is added when the loop returns.
+// update launch).  Form 2 (default): the operator launch of iteration k adds
+// alpha_{k-1} p_{k-1} to x, so the update launch moves only r and Ap, and the
+// last step's alpha p is added when the loop returns; form 1: the update
+// launch adds alpha p to x.
 // Convergence (and, in reliable mode, the need for an FP64 residual
 // replacement) is decided on the device; the host reads the state after each
 // batch of iterations.  Returns with h->st_host[sid] current.
@@ -133,6 +134,9 @@ int cg_loop(sdg_handle* h, const Op& op, T* x, T* const* r, T* const* p, T* cons
   SolverState* st = st_dev(h, sid);
   double* pa = parts(h, sid);
   const long long n = h->g.ndof;
+  // two-launch forms: x += alpha p in the operator launch (form 2) or in the
+  // update launch (form 1, and always with the FP32 kernel deflation)
+  const bool xop = !fused && h->form == 2 && !deflate;
   // buffers alternate with the executed iteration; launches skipped after a
   // pause or convergence do not count, so j restarts from the device count
   long long launched = h->st_host[sid].iter;
@@ -167,18 +171,18 @@ int cg_loop(sdg_handle* h, const Op& op, T* x, T* const* r, T* const* p, T* cons
         a.fuse = 1;
         a.x = r[0];
         a.y = Ap[0];
-        a.xsol = x;
+        a.xsol = xop ? x : nullptr;
         a.kc = deflate ? h->kc : nullptr;
       }
       if (prof) SDG_CK(cudaEventRecord(h->pev[2 * k], s));
       if constexpr (sizeof(T) == 8) {
         SDG_K(launch_apply_f64(h, a, s));
         if (prof) SDG_CK(cudaEventRecord(h->pev[2 * k + 1], s));
-        if (!fused) SDG_K(cg_update_f64(nullptr, r[0], nullptr, Ap[0], n, st, pa, s));
+        if (!fused) SDG_K(cg_update_f64(xop ? nullptr : x, r[0], p[j1], Ap[0], n, st, pa, h->nsm, s));
       } else {
         SDG_K(launch_apply_f32(h, a, s));
         if (prof) SDG_CK(cudaEventRecord(h->pev[2 * k + 1], s));
-        if (!fused) SDG_K(cg_update_f32(nullptr, r[0], nullptr, Ap[0], n, st, pa, df, s));
+        if (!fused) SDG_K(cg_update_f32(xop ? nullptr : x, r[0], p[j1], Ap[0], n, st, pa, df, h->nsm, s));
       }
       ++launched;
     }
@@ -205,7 +209,7 @@ int cg_loop(sdg_handle* h, const Op& op, T* x, T* const* r, T* const* p, T* cons
     if (segment_cap > 0 && hs.iter - iter_start >= segment_cap) break;  // caller replaces the residual
     if (batch < 32) batch *= 2;
   }
-  if (!fused) {
+  if (xop) {
     // the last operator launch (iteration iter - 1) wrote p[iter & 1]; its
     // alpha p is still to be added to x (no-op after a breakdown: alpha 0)
     SDG_K(pending_x(x, p[h->st_host[sid].iter & 1], n, st, s));
@@ -307,7 +311,7 @@ int solve_reliable(sdg_handle* h, const Op& op, const double* b, double* x, doub
   const int unscaled = fp32 ? 0 : 1;
   // one launch per iteration unless asked otherwise or the FP32 iteration
   // deflates the kernel
-  const bool fused = !deflate && !h->two_launch;
+  const bool fused = !deflate && h->form == 0;
   double* r64v[2] = {h->r64, fused ? h->r64b : h->r64};
   double* Ap64v[2] = {h->Ap64, fused ? h->Ap64b : h->Ap64};
   float* r32v[2] = {h->r32, fused ? h->r32b : h->r32};
@@ -615,7 +619,7 @@ int sdg_create(const sdg_grid* grid, int N, double nu, double theta, double dt, 
   h->delta = 0.5;
   h->nsub = 1;
   h->tile32 = 0;
-  h->two_launch = 1;  // measured faster than the one-launch form (2D and 3D)
+  h->form = 2;  // measured faster than the other forms (2D and 3D)
   h->maxit = 1000000;
   h->max_updates = 10000;
   build_basis(N, &h->basis);
@@ -772,8 +776,8 @@ int sdg_set_convection_substeps(sdg_handle* h, int nsub) {
 
 int sdg_set_iteration_form(sdg_handle* h, int form) {
   SDG_ARG(h, "NULL handle");
-  SDG_ARG(form == 0 || form == 1, "iteration form must be 0 or 1");
-  h->two_launch = form;
+  SDG_ARG(form >= 0 && form <= 2, "iteration form must be 0, 1 or 2");
+  h->form = form;
   return SDG_OK;
 }
 

@@ -387,6 +387,10 @@ __global__ void __launch_bounds__(Tile<DIM, N1, TV>::THREADS, (apply_min_blocks<
   const int VZ = DIM == 3 ? min(TZ, a.n[2] - o[2]) : 1;
 
   if (threadIdx.x < N1) s_w[threadIdx.x] = a.w[threadIdx.x];
+  // 2D tile fully inside the grid, elements of whole vectors: staging and
+  // store take the element of each vector from its position (no slot table)
+  const bool fast2 = DIM == 2 && !fuse2 && !defl && VW > 1 && VX == TX && VY == TY;
+  if (!fast2)
   for (int sl = threadIdx.x; sl < NSLOT; sl += blockDim.x) {
     int g[3];
     s_gel[sl] = slot_elem<DIM, TX, TY, TZ>(sl, o, VX, VY, VZ, a.n, g)
@@ -459,6 +463,52 @@ __global__ void __launch_bounds__(Tile<DIM, N1, TV>::THREADS, (apply_min_blocks<
       }
     }
   }
+  if (fast2) {
+    constexpr int RV = TX * NV;  // vectors in one box row of TX elements
+    const int nx = a.n[0], ny = a.n[1];
+    // one vector of the value the passes read: x (plain) or p = r + beta
+    // p_old (CG; owned: stored, and x += alpha p_old), into slot at off
+    auto stage2 = [&](size_t gi, bool owned, int slot, int off) {
+      V val = reinterpret_cast<const V*>(a.x)[gi];
+      if (fuse && !first) {
+        const V po = reinterpret_cast<const V*>(a.p_old)[gi];
+        T* vp = reinterpret_cast<T*>(&val);
+        const T* pp = reinterpret_cast<const T*>(&po);
+#pragma unroll
+        for (int k = 0; k < VW; ++k) vp[k] = vp[k] + beta * pp[k];
+        if (owned && xupd) {
+          V xv = reinterpret_cast<const V*>(a.xsol)[gi];
+          T* xp = reinterpret_cast<T*>(&xv);
+#pragma unroll
+          for (int k = 0; k < VW; ++k) xp[k] = fma(alpha, pp[k], xp[k]);
+          reinterpret_cast<V*>(a.xsol)[gi] = xv;
+        }
+      }
+      if (fuse && owned) reinterpret_cast<V*>(a.p_out)[gi] = val;
+      const T* vp = reinterpret_cast<const T*>(&val);
+#pragma unroll
+      for (int k = 0; k < VW; ++k) {
+        const int q = off * VW + k, row = q / N1, l1 = q - row * N1;
+        s_in[slot * ES + row * RS + l1] = vp[k];
+      }
+    };
+    for (int v = threadIdx.x; v < TY * RV; v += TS::THREADS) {  // box rows
+      const int row = v / RV, i = v - row * RV, e = i / NV;
+      stage2(((size_t)(o[1] + row) * nx + o[0]) * NV + i, true, row * TX + e, i - e * NV);
+    }
+    for (int v = threadIdx.x; v < 2 * RV; v += TS::THREADS) {  // y = -1, y = TY rows
+      const int side = v / RV, i = v - side * RV, e = i / NV;
+      int gy = side ? o[1] + TY : o[1] - 1;
+      gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
+      stage2(((size_t)gy * nx + o[0]) * NV + i, false, TE + 2 * TY + side * TX + e, i - e * NV);
+    }
+    for (int v = threadIdx.x; v < 2 * TY * NV; v += TS::THREADS) {  // x = -1, x = TX columns
+      const int sl = v / NV, off = v - sl * NV, side = sl / TY, ly = sl - side * TY;
+      int gx = side ? o[0] + TX : o[0] - 1;
+      gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
+      stage2(((size_t)(o[1] + ly) * nx + gx) * NV + off, false, TE + sl, off);
+    }
+  } else
   for (int v = threadIdx.x + (fuse2 ? TE * NV : 0); v < NSLOT * NV; v += blockDim.x) {
     const int s = v / NV, off = v - s * NV;
     const int ge = s_gel[s];
@@ -632,7 +682,7 @@ __global__ void __launch_bounds__(Tile<DIM, N1, TV>::THREADS, (apply_min_blocks<
   const int vstep = WARP_ELEMS ? 32 : blockDim.x;
   for (int v = v0; v < v1; v += vstep) {
     const int e = v / NV, off = v - e * NV;
-    const int ge = s_gel[e];
+    const int ge = fast2 ? (o[1] + e / TX) * a.n[0] + o[0] + e % TX : s_gel[e];
     if (ge < 0) continue;
     V yv, pv;
     T* yp = reinterpret_cast<T*>(&yv);
@@ -655,31 +705,11 @@ __global__ void __launch_bounds__(Tile<DIM, N1, TV>::THREADS, (apply_min_blocks<
     }
   }
   if (fuse) {
-    double tot[1];
-    bool last;
-    if constexpr (sizeof(T) == 4) {
-      F2 v1[1] = {F2{(float)dsum, -(float)dcomp}};
-      last = grid_sum_f2<1>(v1, a.partials, &a.st->counter, tot);
-    } else {
-      double v1[1] = {(double)dsum - (double)dcomp};
-      last = grid_sum<1>(v1, a.partials, &a.st->counter, tot);
-    }
-    if (last) {
-      if (threadIdx.x == 0) {
-        SolverState* st = a.st;
-        const double pAp = tot[0];
-        st->pAp = pAp;
-        if (!(pAp > 0.0) || !isfinite(pAp)) {
-          st->done = 1;
-          st->status = SDG_ERR_BREAKDOWN;
-          st->alpha = 0.0;
-        } else {
-          st->alpha = st->rr / pAp;
-        }
-        st->alpha_f = (float)st->alpha;
-        if (a.xsol != nullptr) st->xpend = 1;  // x lacks alpha_k p_k
-      }
-    }
+    // the block's p.Ap total for the update launch, which forms alpha
+    __shared__ double s_opr[32];
+    if constexpr (sizeof(T) == 4) op_partial_f2(F2{(float)dsum, -(float)dcomp}, a.partials, s_opr);
+    else op_partial_f64((double)dsum - (double)dcomp, a.partials, s_opr);
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.st->nop = (int)gridDim.x;
   }
 }
 

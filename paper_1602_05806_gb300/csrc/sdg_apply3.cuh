@@ -488,29 +488,11 @@ __global__ void __launch_bounds__(March3<N1>::THREADS, (march3_min_blocks<T, ONE
     }
     if (last && threadIdx.x == 0) cg_iteration_finish(a.st, tot[0], tot[1], tot[2], tot[3]);
   } else {
-    double tot[1];
-    bool last;
-    if constexpr (sizeof(T) == 4) {
-      F2 v1[1] = {F2{(float)s_pa, -(float)c_pa}};
-      last = grid_sum_f2<1>(v1, a.partials, &a.st->counter, tot);
-    } else {
-      double v1[1] = {(double)s_pa - (double)c_pa};
-      last = grid_sum<1>(v1, a.partials, &a.st->counter, tot);
-    }
-    if (last && threadIdx.x == 0) {
-      SolverState* st = a.st;
-      const double pAp = tot[0];
-      st->pAp = pAp;
-      if (!(pAp > 0.0) || !isfinite(pAp)) {
-        st->done = 1;
-        st->status = SDG_ERR_BREAKDOWN;
-        st->alpha = 0.0;
-      } else {
-        st->alpha = st->rr / pAp;
-      }
-      st->alpha_f = (float)st->alpha;
-      if (a.xsol != nullptr) st->xpend = 1;  // x lacks alpha_k p_k
-    }
+    // the block's p.Ap total for the update launch, which forms alpha
+    __shared__ double s_opr[32];
+    if constexpr (sizeof(T) == 4) op_partial_f2(F2{(float)s_pa, -(float)c_pa}, a.partials, s_opr);
+    else op_partial_f64((double)s_pa - (double)c_pa, a.partials, s_opr);
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.st->nop = (int)gridDim.x;
   }
 }
 

@@ -160,6 +160,54 @@ __device__ __forceinline__ bool grid_sum_f2(F2 (&v)[K], double* partials, unsign
   return true;
 }
 
+// ---- operator totals handed to the next launch ------------------------------
+// The operator launch of a two-launch CG iteration ends without a grid-wide
+// finish: each block leaves its p.Ap total in slot kOpSlot of its partials
+// row (FP32 data: as a float pair), and every block of the update launch adds
+// them in the same fixed order, so that no serial last-block step sits
+// between the two launches.
+constexpr int kOpSlot = 2;
+
+// Block total of an FP32 operator block (float pair) into its partials row.
+// All threads of the block must call it.
+__device__ __forceinline__ void op_partial_f2(F2 v, double* partials, double* s_red) {
+  F2 a[1] = {v};
+  double b[1];
+  block_sum_f2<1>(a, s_red, b);
+  if (threadIdx.x == 0) {
+    const float hi = (float)b[0];
+    const float lo = (float)(b[0] - (double)hi);
+    *reinterpret_cast<float2*>(partials + (size_t)blockIdx.x * kPartialSlots + kOpSlot) = make_float2(hi, lo);
+  }
+}
+__device__ __forceinline__ void op_partial_f64(double v, double* partials, double* s_red) {
+  double a[1] = {v}, b[1];
+  block_sum<1>(a, s_red, b);
+  if (threadIdx.x == 0) partials[(size_t)blockIdx.x * kPartialSlots + kOpSlot] = b[0];
+}
+
+// The sum of the n operator totals, the same in every thread of every block
+// (fixed order: thread t adds totals t, t + blockDim, ..., then the block
+// tree).  All threads of the block must call it.
+__device__ __forceinline__ double sum_op_partials_f2(const double* partials, int n, double* s_red) {
+  F2 a{0.0f, 0.0f};
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float2 q = __ldcg(reinterpret_cast<const float2*>(partials + (size_t)i * kPartialSlots + kOpSlot));
+    a = f2_add(a, F2{q.x, q.y});
+  }
+  F2 v[1] = {a};
+  double out[1];
+  block_sum_f2<1>(v, s_red, out);
+  return out[0];
+}
+__device__ __forceinline__ double sum_op_partials_f64(const double* partials, int n, double* s_red) {
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += __ldcg(&partials[(size_t)i * kPartialSlots + kOpSlot]);
+  double v[1] = {a}, out[1];
+  block_sum<1>(v, s_red, out);
+  return out[0];
+}
+
 // ---- programmatic dependent launch -----------------------------------------
 // A kernel launched with programmatic stream serialisation may start while
 // the previous kernel of the stream finishes.  pdl_trigger lets the next

@@ -37,6 +37,8 @@ struct SolverState {
   int updates;      // reliable updates done
   int xpend;        // two-launch form: 1 while x lacks alpha p of the last operator launch
                     // (the next operator launch adds it, or the CG loop when it returns)
+  int nop;          // two-launch form: blocks of the last operator launch (their p.Ap totals
+                    // wait in the partials for the update launch)
   unsigned int counter;  // last-block ticket counter (reset by the last block)
 };
 
@@ -74,7 +76,7 @@ struct sdg_handle {
   double nu, theta, dt;
   int nsub;                      // SSP-RK3 sub-steps of the explicit convection per dt
   int tile32;                    // tile shape variant of the 2D FP32 operator
-  int two_launch;                // CG iteration form: 1 = operator + update launches
+  int form;                      // CG iteration form: 0 one launch, 1 / 2 operator + update launches
   int precision;
   double rtol_p, rtol_v;
   double delta;     // mixed: reliable-update factor
@@ -195,11 +197,14 @@ cudaError_t apply_dispatch_3d(const sdg_handle* h, const ApplyArgs<double>& a, c
 cudaError_t apply_dispatch_3d(const sdg_handle* h, const ApplyArgs<float>& a, cudaStream_t s);
 
 // ---- vector / step kernels (sdg_kernels.cu) --------------------------------
-// (x may be null: x += alpha p is then left to the next operator launch)
+// Update launch of a two-launch CG iteration: alpha from the operator
+// blocks' p.Ap totals (slot kOpSlot of partials), r -= alpha Ap, r.r, and
+// the iteration's decisions; x += alpha p too unless x is null (then the next
+// operator launch adds it).  nsm: SMs of the device (grid of one wave).
 cudaError_t cg_update_f64(double* x, double* r, const double* p, const double* Ap, long long n,
-                          SolverState* st, double* partials, cudaStream_t s);
+                          SolverState* st, double* partials, int nsm, cudaStream_t s);
 cudaError_t cg_update_f32(float* x, float* r, const float* p, const float* Ap, long long n,
-                          SolverState* st, double* partials, const Deflate& df, cudaStream_t s);
+                          SolverState* st, double* partials, const Deflate& df, int nsm, cudaStream_t s);
 // FP32 CG with FP64 reliable updates:
 //   rel_accumulate: x64 += x32 / sigma, x32 = 0
 //   rel_residual:   r64 = b - Ax (FP64), mean and ||r - mean|| reduced in FP64;

@@ -25,8 +25,9 @@ def main(argv=None):
     ap.add_argument("--dim", type=int, default=2)
     ap.add_argument("--iters", type=int, default=40)
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
-    ap.add_argument("--form", type=int, choices=[0, 1], default=1,
-                    help="CG iteration form: 0 one launch per iteration, 1 operator + update")
+    ap.add_argument("--form", type=int, choices=[0, 1, 2], default=2,
+                    help="CG iteration form: 0 one launch per iteration, 1 operator + update (x in the update), "
+                         "2 operator + update (x in the operator launch)")
     ap.add_argument("--delta", type=float, default=0.5,
                     help="mixed: reliable-update factor (small: no residual replacement within the run, so "
                          "every captured launch is a full iteration)")

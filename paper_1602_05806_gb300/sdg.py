@@ -251,7 +251,8 @@ class Handle:
         check(lib().sdg_set_convection_substeps(self.h, int(nsub)))
 
     def set_iteration_form(self, form):
-        """0: one launch per CG iteration (default); 1: operator + update launches."""
+        """0: one launch per CG iteration; 1: operator + update launches, x += alpha p in the update;
+        2 (default): operator + update launches, x += alpha p in the next operator launch."""
         check(lib().sdg_set_iteration_form(self.h, int(form)))
 
     def set_tile(self, variant):

@@ -122,6 +122,35 @@ def test_pressure_cg_mixed(dim, n, N):
     assert rel(xg, ref.x) <= 1e-10
 
 
+@pytest.mark.parametrize("form", [0, 1, 2])
+@pytest.mark.parametrize("dim,n,N", [(2, (9, 6), 3), (3, (8, 6, 7), 4)])
+def test_iteration_forms(dim, n, N, form):
+    """The three device forms of a CG iteration (one launch; two launches
+    with x += alpha p in the update launch; two launches with it in the next
+    operator launch) solve to the oracle's exact solution in FP64 and mixed
+    precision, and a capped FP64 solve keeps the iterate of plain CG after
+    three iterations (the x bookkeeping of each form at the cap)."""
+    o, h = make(dim, n, N)
+    h.set_iteration_form(form)
+    rng = np.random.default_rng(70 + N)
+    b = o.pressure_apply(rng.standard_normal(o.shape))
+    x0 = rng.standard_normal(o.shape)
+    ex = o.pressure_solve_exact(b, x0)
+    for prec, tol in ((sdg.SDG_FP64, 1e-11), (sdg.SDG_MIXED, 1e-10)):
+        h.set_options(prec, 1e-13, 1e-13, 1000000)
+        X = dev(x0)
+        info = h.pressure_cg(dev(b), X)
+        assert info["status"] == sdg.SDG_OK, (prec, info)
+        assert info["true_res"] <= max(1e-13, 10.0 * info["floor_res"]), (prec, info)
+        assert rel(host(X), ex) <= tol, prec
+    h.set_options(sdg.SDG_FP64, 1e-14, 1e-14, 3)
+    X = dev(x0)
+    info = h.pressure_cg(dev(b), X, ok=(sdg.SDG_OK, sdg.SDG_ERR_NOT_CONVERGED))
+    assert info["status"] == sdg.SDG_ERR_NOT_CONVERGED and info["iters"] == 3
+    ref = cg(o.pressure_apply, b, x0, 1e-30, maxit=3)
+    assert rel(host(X), ref.x) <= 1e-12
+
+
 @pytest.mark.parametrize("N", [1, 3, 7, 10])
 def test_tile_variants_apply_and_mixed_cg(N):
     """Every tile shape of the 2D FP32 operator (base, wide in x, wide in y)
