@@ -188,12 +188,21 @@ __device__ __forceinline__ void op_partial_f64(double v, double* partials, doubl
 
 // The sum of the n operator totals, the same in every thread of every block
 // (fixed order: thread t adds totals t, t + blockDim, ..., then the block
-// tree).  All threads of the block must call it.
+// tree).  The loads go out in batches of eight, so that their latencies
+// overlap.  All threads of the block must call it.
 __device__ __forceinline__ double sum_op_partials_f2(const double* partials, int n, double* s_red) {
+  constexpr int B = 8;
   F2 a{0.0f, 0.0f};
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const float2 q = __ldcg(reinterpret_cast<const float2*>(partials + (size_t)i * kPartialSlots + kOpSlot));
-    a = f2_add(a, F2{q.x, q.y});
+  for (int i0 = threadIdx.x; i0 < n; i0 += B * blockDim.x) {
+    float2 q[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int i = i0 + b * blockDim.x;
+      q[b] = i < n ? __ldcg(reinterpret_cast<const float2*>(partials + (size_t)i * kPartialSlots + kOpSlot))
+                   : make_float2(0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) a = f2_add(a, F2{q[b].x, q[b].y});
   }
   F2 v[1] = {a};
   double out[1];
@@ -201,8 +210,18 @@ __device__ __forceinline__ double sum_op_partials_f2(const double* partials, int
   return out[0];
 }
 __device__ __forceinline__ double sum_op_partials_f64(const double* partials, int n, double* s_red) {
+  constexpr int B = 8;
   double a = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) a += __ldcg(&partials[(size_t)i * kPartialSlots + kOpSlot]);
+  for (int i0 = threadIdx.x; i0 < n; i0 += B * blockDim.x) {
+    double q[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int i = i0 + b * blockDim.x;
+      q[b] = i < n ? __ldcg(&partials[(size_t)i * kPartialSlots + kOpSlot]) : 0.0;
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) a += q[b];
+  }
   double v[1] = {a}, out[1];
   block_sum<1>(v, s_red, out);
   return out[0];

@@ -99,6 +99,32 @@ __global__ void __launch_bounds__(kThreads, DEFL ? 1 : 4)
   pdl_trigger();
   pdl_wait();  // the p.Ap totals and Ap come from the operator kernel just before
   if (st->done || st->pause) return;
+  using V = typename V4<T>::V;
+  constexpr int W = V4<T>::W;
+  const long long nv = n / W;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  // U vectors per thread and pass, all loads issued before the arithmetic
+  // (the update is bound by memory latency, not bandwidth, at one vector);
+  // the first pass's loads go out before alpha is formed
+  constexpr int U = 2;
+  constexpr bool withx = WITHX;
+  V xv[U], rv[U], pv[U], av[U];
+  auto issue = [&](long long i0) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long i = i0 + u * nth;
+      if (i < nv) {
+        if (withx) {
+          xv[u] = reinterpret_cast<V*>(x)[i];
+          pv[u] = reinterpret_cast<const V*>(p)[i];
+        }
+        rv[u] = reinterpret_cast<V*>(r)[i];
+        av[u] = reinterpret_cast<const V*>(Ap)[i];
+      }
+    }
+  };
+  issue(tid);
   // alpha = r.r / p.Ap from the operator blocks' totals (every block forms the
   // same value; one FP64 division per block)
   __shared__ double s_opr[32];
@@ -115,31 +141,10 @@ __global__ void __launch_bounds__(kThreads, DEFL ? 1 : 4)
     for (int l = threadIdx.x; l < df.npe; l += blockDim.x) s_k[l] = 0.0f;
     __syncthreads();
   }
-  using V = typename V4<T>::V;
-  constexpr int W = V4<T>::W;
   const T alpha = sizeof(T) == 4 ? (T)(float)s_alpha : (T)s_alpha;
   DotAcc<T> rr;
-  const long long nv = n / W;
-  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long nth = (long long)gridDim.x * blockDim.x;
-  // U vectors per thread and pass, all loads issued before the arithmetic
-  // (the update is bound by memory latency, not bandwidth, at one vector)
-  constexpr int U = 2;
-  constexpr bool withx = WITHX;
   for (long long i0 = tid; i0 < nv; i0 += U * nth) {
-    V xv[U], rv[U], pv[U], av[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const long long i = i0 + u * nth;
-      if (i < nv) {
-        if (withx) {
-          xv[u] = reinterpret_cast<V*>(x)[i];
-          pv[u] = reinterpret_cast<const V*>(p)[i];
-        }
-        rv[u] = reinterpret_cast<V*>(r)[i];
-        av[u] = reinterpret_cast<const V*>(Ap)[i];
-      }
-    }
+    if (i0 != tid) issue(i0);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const long long i = i0 + u * nth;
