@@ -39,7 +39,9 @@ METRIC = "pressure-CG GDOF/s & s/time-step, mixed vs FP64 at <=1e-10 rel err; % 
 WORKLOAD = "tg2d_256x256_N7"
 CPU_SAMPLE_CELLS = (32, 32)      # oracle sample: same degree / parameters, 32 x 32 cells
 FLUSH_BYTES = 512 << 20          # > 129 MB L2
-BYTES_PER_DOF_FUSED_F32 = 16     # fused CG operator: read r, p_old; write p, Ap (FP32)
+# fused CG operator of the default iteration form (FP32): read r, p_old, x;
+# write p, Ap, x (x += alpha p_old of the previous iteration rides along)
+BYTES_PER_DOF_FUSED_F32 = 24
 
 
 def parse():
@@ -355,8 +357,8 @@ def run_ours(args):
     else:
         roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
                     "frac": frac_alu, "traffic": traffic}
-    roofline.update({"kernel": "k_apply<float,2,8> (fused CG: p = r + beta p, A p, p.Ap; timed in one "
-                               "extra step with events around each launch)",
+    roofline.update({"kernel": "k_apply<float,2,8> (fused CG operator: x += alpha p_old, p = r + beta p_old, "
+                               "A p, p.Ap; timed in one extra step with events around each launch)",
                      "avg_launch_us": avg_ms * 1e3, "launches_timed": n32,
                      "peak_source": peak_src + (" (hbm_gbs)" if roofline["bound"] == "hbm"
                                                 else " (152 SM x 128 FP32 lanes x 2 x sm_max_mhz)"),
@@ -489,7 +491,8 @@ def run_ours(args):
                 "kinetic_energy_mixed_vs_fp64_max_rel": dK,
                 "roofline": {"bound": "hbm", "achieved": ach3, "peak": hbm_peak3, "unit": "GB/s",
                              "frac": ach3 / hbm_peak3, "traffic": ncu_traffic("tg3d_48_N4"),
-                             "kernel": "k_apply3m<float,5> (fused z-marching CG operator; events around each launch "
+                             "kernel": "k_apply3m<float,5> (fused z-marching CG operator: x += alpha p_old, "
+                                       "p = r + beta p_old, A p, p.Ap; events around each launch "
                                        "in one extra mixed step)",
                              "avg_launch_us": avg3 * 1e3, "launches_timed": n3,
                              "algorithmic_bytes_per_launch": b3}}

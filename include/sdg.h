@@ -387,10 +387,9 @@ int sdg_diagnostics(sdg_handle* h, double* kinetic_energy, double* div_norm,
 
 /* Kinetic energy K = (1/|Omega|) int |v|^2 / 2 of caller-owned velocity
  * arrays, like the kinetic_energy output of sdg_diagnostics, for callers that
- * cannot allocate device memory: code recording a CUDA graph (an allocation
- * while a stream is captured is an error), code whose device memory is owned
- * by another allocator or pool, and latency-critical loops where an
- * allocation would stall the device.  The paper has no counterpart; it is a
+ * cannot allocate device memory: code whose device memory is owned by another
+ * allocator or pool, and latency-critical loops where an allocation would
+ * stall the device.  The paper has no counterpart; it is a
  * service of this library.
  *   - Needs no handle and calls no cudaMalloc, cudaFree or allocating
  *     library routine.  Its scratch (partial sums and a ticket counter) is a
@@ -405,8 +404,7 @@ int sdg_diagnostics(sdg_handle* h, double* kinetic_energy, double* div_norm,
  *   - The first call in each CUDA context of a device looks up the scratch
  *     array's device address (cudaGetSymbolAddress) with that device
  *     current, and keeps it for later calls in the same context (a new
- *     context, e.g. after cudaDeviceReset, repeats the look-up); make that
- *     first call before any stream capture.
+ *     context, e.g. after cudaDeviceReset, repeats the look-up).
  *   - Every call shares the one scratch array: calls that can overlap on the
  *     GPU (different streams, or different host threads) race and must be
  *     ordered by the caller.  Each call clears the counter it relies on.

@@ -1,10 +1,8 @@
 // Allocation-free kinetic-energy reduction (sdg_kinetic_energy_noalloc).
 //
-// Some callers cannot call cudaMalloc: code running while a stream is being
-// captured into a CUDA graph (an allocation there is an error), code whose
-// device memory is owned by another allocator or pool that must not grow or
-// fragment, and latency-critical loops where an allocation would stall the
-// device.  For them this entry point needs no handle and allocates nothing:
+// Some callers cannot call cudaMalloc: code whose device memory is owned by
+// another allocator or pool that must not grow or fragment, and
+// latency-critical loops where an allocation would stall the device.  For them this entry point needs no handle and allocates nothing:
 // its scratch (the per-block partial sums and the ticket counter of the
 // last-block reduction) is the file-scope array below, which every GPU that
 // loads the library holds until the process exits.

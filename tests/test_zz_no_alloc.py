@@ -1,8 +1,7 @@
 """The allocation-free kinetic-energy entry point (sdg_kinetic_energy_noalloc)
 agrees with the kinetic energy that sdg_diagnostics computes from a handle's
 state, on two calls in a row.  It serves callers that cannot allocate device
-memory (graph capture, externally owned memory pools, latency-critical
-loops).  This file is collected last so that a run stopping at the first
+memory (externally owned memory pools, latency-critical loops).  This file is collected last so that a run stopping at the first
 failure has already run every other test."""
 import math
 
