@@ -12,7 +12,8 @@
 // warp use the same matrix entry at the same instruction, so the blocks are
 // read straight from the kernel-parameter constant bank.  Partial results of
 // the passes meet in a shared-memory accumulator; the last step stores the
-// box with vector stores and (CG mode) reduces p^T A p.
+// box with vector stores and (CG mode) leaves the block's p^T A p total for
+// the update launch, which forms alpha (no grid-wide finish here).
 #pragma once
 
 #include <atomic>

@@ -13,7 +13,8 @@
 // them, and each plane is stored as it is finished.
 //
 // Modes as in k_apply: plain apply (fuse 0), the operator of the two-launch
-// CG iteration (fuse 1: p = r + beta p_old, p.Ap) and the one-launch CG
+// CG iteration (fuse 1: p = r + beta p_old, x += alpha p_old when the state
+// asks for it, and the block's p.Ap total for the update launch) and the one-launch CG
 // iteration (ONE: r -= alpha Ap_old, x += alpha p_old, p = r + beta p_old,
 // Ap, and p.Ap, r.r, r.Ap, Ap.Ap).  Planes z0 - 1 and z0 + zc belong to the
 // neighbouring runs: this CTA forms their values but writes nothing there.
