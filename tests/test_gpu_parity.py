@@ -151,6 +151,25 @@ def test_iteration_forms(dim, n, N, form):
     assert rel(host(X), ref.x) <= 1e-12
 
 
+@pytest.mark.parametrize("dim,n,N", [(2, (9, 6), 3), (2, (8, 8), 5)])
+def test_mixed_cg_with_kernel_deflation(dim, n, N):
+    """Mixed CG with the FP32 iterations' kernel deflation switched on (the
+    operator builds each direction from the residual's range part and the
+    update removes the kernel part of r.r): converges to the oracle's exact
+    solution like the default solver."""
+    o, h = make(dim, n, N)
+    rng = np.random.default_rng(90 + N)
+    b = o.pressure_apply(rng.standard_normal(o.shape))
+    x0 = rng.standard_normal(o.shape)
+    h.set_options(sdg.SDG_MIXED, 1e-13, 1e-13, 1000000)
+    h.set_mixed_options(0.1, 1000, deflate=True)
+    X = dev(x0)
+    info = h.pressure_cg(dev(b), X)
+    assert info["status"] == sdg.SDG_OK, info
+    assert info["true_res"] <= max(1e-13, 10.0 * info["floor_res"]), info
+    assert rel(host(X), o.pressure_solve_exact(b, x0)) <= 1e-10
+
+
 @pytest.mark.parametrize("N", [1, 3, 7, 10])
 def test_tile_variants_apply_and_mixed_cg(N):
     """Every tile shape of the 2D FP32 operator (base, wide in x, wide in y)
